@@ -1,0 +1,189 @@
+"""Pins of the oracle's time stepping against closed forms (Sec. 3b), the linear stability
+analysis of App. A and the stability facts the paper reports (Secs. 4b, 4c, 5a)."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import collision, lbm, lsa, d2q9
+from paper_2002_05265_gb300 import flows
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+CS = np.sqrt(d2q9.CS2)
+
+
+def _shear_amplitude(f, L, k):
+    _, _, uy = collision.macroscopic(f)
+    return 2.0 / L * (uy.mean(axis=0) * np.sin(k * np.arange(L))).sum()
+
+
+def _measured_shear_rate(model, nu, L, t1, t2):
+    rates = lbm.rates_from_nu(nu, "srt")
+    rho, ux, uy = flows.shear_wave(L, 4, amp=1e-4)
+    f = lbm.init_equilibrium(rho, ux, uy)
+    k = 2 * np.pi / L
+    f = lbm.run(f, model, rates, t1)
+    a1 = _shear_amplitude(f, L, k)
+    f = lbm.run(f, model, rates, t2 - t1)
+    a2 = _shear_amplitude(f, L, k)
+    return np.log(a1 / a2) / (t2 - t1)
+
+
+@pytest.mark.parametrize("nu,t1,t2", [(1e-3, 400, 1400), (1e-2, 200, 600), (1e-1, 100, 400)])
+def test_shear_wave_decays_at_nu_k2(nu, t1, t2):
+    """Sec. 3b: Im(omega_S) = -nu k^2, with omega_nu = 1/(nu/c_s^2 + 1/2) (Sec. 4c).
+    Measured BGK decay rate within 1 % of nu k^2 at L = 64."""
+    L = 64
+    rate = _measured_shear_rate("bgk", nu, L, t1, t2)
+    assert rate == pytest.approx(nu * (2 * np.pi / L) ** 2, rel=1e-2)
+
+
+def _shear_eigen_rate(model, nu, k):
+    G = lsa.collision_map_jacobian(model, 1.0, 0.0, 0.0, lbm.rates_from_nu(nu, "srt"))
+    om = lsa.omegas(G, k, 0.0)
+    hydro = om[np.abs(om.real) < 1e-9]           # at rest the shear mode does not propagate
+    return -np.max(hydro.imag)
+
+
+@pytest.mark.parametrize("model", collision.MODELS)
+@pytest.mark.parametrize("nu,t1,t2", [(1e-2, 300, 700), (1e-1, 100, 400)])
+def test_shear_wave_matches_discrete_eigenvalue(model, nu, t1, t2):
+    """The measured decay of the time-stepped shear wave equals the shear eigenvalue of
+    M^D(k) (Eq. EigenvaluePbDiscrete) to 1e-6 relative."""
+    L = 64
+    rate = _measured_shear_rate(model, nu, L, t1, t2)
+    assert rate == pytest.approx(_shear_eigen_rate(model, nu, 2 * np.pi / L), rel=1e-6)
+
+
+def test_small_k_dispersion_matches_linearised_navier_stokes():
+    """Sec. 3b: Re(omega_S) = u k, Re(omega_pm) = (u pm c_s) k, Im = -nu k^2 (nu_b = nu)."""
+    nu, Ma = 1e-3, 0.1
+    u = Ma * CS
+    k = 1e-3
+    G = lsa.collision_map_jacobian("bgk", 1.0, u, 0.0, lbm.rates_from_nu(nu))
+    om = lsa.omegas(G, k, 0.0)
+    hyd = sorted(om[np.abs(om.imag) < 10 * nu * k * k], key=lambda z: z.real)
+    assert len(hyd) == 3
+    np.testing.assert_allclose([z.real for z in hyd], [(u - CS) * k, u * k, (u + CS) * k], rtol=1e-4)
+    np.testing.assert_allclose([-z.imag for z in hyd], [nu * k * k] * 3, rtol=2e-2)
+
+
+def test_linearised_step_spectrum_equals_union_of_fourier_blocks():
+    """App. A: the Jacobian of one full stream-and-collide step about a uniform flow on an
+    8 x 8 periodic lattice has the eigenvalues of E^D(k)[delta + J] over the 64 lattice
+    wavenumbers (checks the sign convention exp(-i xi.k) against the streaming)."""
+    L = 8
+    model, rates, ux, uy = "chm", (1.6, 1.0, 1.0), 0.15, -0.05
+    base = lbm.init_equilibrium(np.ones((L, L)), np.full((L, L), ux), np.full((L, L), uy)).astype(complex)
+    n = 9 * L * L
+    Jfull = np.zeros((n, n))
+    h = 1e-30
+    for col in range(n):
+        fp = base.copy().reshape(-1)
+        fp[col] += 1j * h
+        Jfull[:, col] = lbm.step(fp.reshape(9, L, L), model, rates).reshape(-1).imag / h
+    big = np.linalg.eigvals(Jfull)
+    G = lsa.collision_map_jacobian(model, 1.0, ux, uy, rates)
+    union = np.concatenate([lsa.eigenvalues(G, 2 * np.pi * a / L, 2 * np.pi * b / L)
+                            for a in range(L) for b in range(L)])
+    d1 = max(np.min(np.abs(union - z)) for z in big)
+    d2 = max(np.min(np.abs(big - z)) for z in union)
+    assert d1 < 1e-7 and d2 < 1e-7
+
+
+def test_small_perturbation_grows_at_the_largest_discrete_rate():
+    """Growth of a 1e-13 perturbation of an unstable uniform flow (BGK, Ma = 0.8, nu = 0.1)
+    on a 16 x 16 lattice equals the largest ln|lambda| over the lattice wavenumbers."""
+    L, Ma, nu = 16, 0.8, 0.1
+    rates = lbm.rates_from_nu(nu)
+    ux = Ma * CS
+    G = lsa.collision_map_jacobian("bgk", 1.0, ux, 0.0, rates)
+    ks = 2 * np.pi * np.arange(L) / L
+    expected = lsa.max_growth_rate(G, ks, ks)
+    assert expected > 0.03
+    base = lbm.init_equilibrium(np.ones((L, L)), np.full((L, L), ux), np.zeros((L, L)))
+    f = base + flows.random_populations_perturbation(base.shape, 1e-13, seed=3)
+    for _ in range(120):
+        f = lbm.step(f, "bgk", rates)
+    n1 = np.linalg.norm(f - base)
+    for _ in range(100):
+        f = lbm.step(f, "bgk", rates)
+    n2 = np.linalg.norm(f - base)
+    assert n2 < 1e-5
+    assert np.log(n2 / n1) / 100 == pytest.approx(expected, rel=2e-3)
+
+
+@pytest.mark.parametrize("model", collision.MODELS)
+@pytest.mark.parametrize("preset", ["srt", "reg"])
+def test_flow_at_rest_is_linearly_stable(model, preset):
+    """Sec. 4b: at Ma = 0 no positive growth rate, nu = 1e-6 (the paper reports an exception
+    for the cumulant model, which the reading taken here does not reproduce; see
+    test_k_is_linearly_identical_to_chm)."""
+    G = lsa.collision_map_jacobian(model, 1.0, 0.0, 0.0, lbm.rates_from_nu(1e-6, preset))
+    ks = np.linspace(-np.pi, np.pi, 33)
+    assert lsa.max_growth_rate(G, ks, ks) < 1e-12
+
+
+def test_second_order_bgk_instability_bubble():
+    """Sec. 5a, Fig. 7: D2Q9-BGK with the second-order equilibrium at Ma = 0.1, nu = 1e-5 has
+    an instability bubble close to k = (0.1, 2.1); the extended equilibrium removes it."""
+    g = GOLDEN["bgk_second_order_instability_bubble"]
+    w = lbm.omega_from_nu(g["nu"])
+    u = g["Ma"] * CS
+    kxs = np.linspace(0.0, 2 * g["kx"], 41)
+    kys = np.linspace(g["ky"] - 0.3, g["ky"] + 0.3, 25)
+    G2 = lsa.collision_map_jacobian("bgk", 1.0, u, 0.0, (w, w, w), eq_order=2)
+    G4 = lsa.collision_map_jacobian("bgk", 1.0, u, 0.0, (w, w, w), eq_order=4)
+    assert lsa.max_growth_rate(G2, kxs, kys) > 1e-4
+    assert lsa.max_growth_rate(G4, kxs, kys) < 0.0
+    # it is a bubble: long waves and the far spectrum stay stable
+    assert lsa.max_growth_rate(G2, np.linspace(0, 0.5, 11), np.linspace(0, 1.0, 11)) < 1e-12
+
+
+def test_critical_mach_number_bounds_bgk_at_high_viscosity():
+    """Secs. 3c, 4c: at high viscosity the LBM recovers the DVBE limit Ma_c = sqrt(3) - 1
+    (about 0.73): BGK with nu = 0.1 is linearly stable at Ma = 0.70 and unstable at 0.75."""
+    mac = GOLDEN["critical_mach_dvbe"]["value"]
+    assert mac == pytest.approx(np.sqrt(3) - 1)
+    w = lbm.omega_from_nu(0.1)
+    ks = np.linspace(-np.pi, np.pi, 41)
+
+    def worst(Ma):
+        return max(lsa.max_growth_rate(lsa.collision_map_jacobian(
+            "bgk", 1.0, Ma * CS * np.cos(p), Ma * CS * np.sin(p), (w, w, w)), ks, ks)
+            for p in np.linspace(0, np.pi / 4, 4))
+    assert worst(0.70) < 1e-12
+    assert worst(0.75) > 1e-3
+
+
+def test_k_is_linearly_identical_to_chm():
+    """Reading of the cumulant model: linearised about a uniform equilibrium, C_22 equals the
+    fourth-order central Hermite moment K~_22 - c_s^2 (K~_20 + K~_02) + c_s^4 rho and the
+    product terms cancel to first order, so K and CHM share one Jacobian for any rates.
+    The paper reports a different linear behaviour for K (unstable at rest, REG-K not
+    improved; Secs. 4b, 4c); that statement is not reproduced and K's parity with the
+    paper's linear results is unpinned."""
+    for (ux, uy) in [(0.0, 0.0), (0.3, 0.1)]:
+        for rates in [(1.9, 1.3, 0.8), (1.99, 1.0, 1.0)]:
+            np.testing.assert_allclose(lsa.collision_map_jacobian("k", 1.0, ux, uy, rates),
+                                       lsa.collision_map_jacobian("chm", 1.0, ux, uy, rates), atol=1e-14)
+    # ... while CM differs from both unless omega4 = omega_nu
+    assert np.max(np.abs(lsa.collision_map_jacobian("k", 1.0, 0.1, 0.0, (1.9, 1.0, 1.0))
+                         - lsa.collision_map_jacobian("cm", 1.0, 0.1, 0.0, (1.9, 1.0, 1.0)))) > 1e-2
+
+
+def test_complex_step_jacobian_matches_central_differences():
+    rates = (1.7, 1.1, 0.9)
+    for model in collision.MODELS:
+        G = lsa.collision_map_jacobian(model, 1.02, 0.2, -0.1, rates)
+        from oracle.equilibrium import feq
+        base = feq(np.array([1.02]), np.array([0.2]), np.array([-0.1]))
+        h = 1e-6
+        for j in range(9):
+            fp, fm = base.copy(), base.copy()
+            fp[j] += h
+            fm[j] -= h
+            col = (collision.collide(model, fp, *rates) - collision.collide(model, fm, *rates))[:, 0] / (2 * h)
+            np.testing.assert_allclose(G[:, j], col, atol=1e-8)
