@@ -1,0 +1,169 @@
+/*
+ * liblbm -- D2Q9 stream-and-collide lattice Boltzmann method on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the one compared in Coreixas, Wissocq, Chopard & Latt, "Impact of
+ * collision models on the physical properties and the stability of lattice Boltzmann
+ * methods" (arXiv:2002.05265):
+ *   f_i(x + xi_i, t + 1) = f*_i(x, t)                       (Eq. StreamCollide)
+ * on a periodic nx x ny lattice (Sec. 5a), with the post-collision populations f* given by
+ * one of the collision models of App. B, all built on the extended equilibrium of
+ * Eq. extendedFeq (Sec. 4c).  Velocity index order (i: xi):
+ *   0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1).
+ *
+ * Conventions for every call below
+ *   Return value   0 (LBM_OK) or a negative LBM_ERR_* code; lbm_last_error() gives detail.
+ *   Pointers       Field arguments are plain pointers to dense row-major arrays
+ *                  [ny][nx] (populations: [9][ny][nx]) of double.  They may point to
+ *                  device memory (the call is then asynchronous on the context's stream
+ *                  and the caller keeps the memory alive until the stream reaches it) or
+ *                  to host memory, pageable or pinned (the call then copies through a
+ *                  device staging buffer owned by the context and, for outputs, waits on
+ *                  the stream before returning).  The library never keeps a caller
+ *                  pointer after a call returns.
+ *   Ownership      The context owns its two population buffers, staging and scratch
+ *                  memory; lbm_destroy frees them.  Callers own every argument array.
+ *   Streams        `cuda_stream` is a cudaStream_t (e.g. torch.cuda.current_stream().
+ *                  cuda_stream); NULL means the legacy default stream.  All work of a
+ *                  context is enqueued on that stream, in call order.
+ *   Threads        A context must not be used from two host threads at once.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Collision models (App. B).  PR is the standard regularized model = HM with
+ * omega3 = omega4 = 1 (Sec. 5c, App. C); the omega3/omega4 passed with PR are ignored. */
+typedef enum {
+    LBM_BGK = 0,   /* f* = f - omega_nu (f - f^eq)                          (Sec. 1)        */
+    LBM_RM  = 1,   /* raw moments relaxed by order                       (Eq. RMcoll)       */
+    LBM_HM  = 2,   /* Hermite moments, then Eq. HM2RM_Q9                    (App. B)        */
+    LBM_CM  = 3,   /* central moments, binomial back-transform              (App. B)        */
+    LBM_CHM = 4,   /* central Hermite moments  (Eqs. CHpoly, CHMcoll, CHM2HM_Q9)            */
+    LBM_K   = 5,   /* cumulants; C22 = K22 - (K20 K02 + 2 K11^2)/rho        (Sec. 4c)       */
+    LBM_PR  = 6,   /* standard regularized (= REG-HM)                       (Sec. 5c)       */
+    LBM_RR  = 7    /* recursive regularized      (Eqs. HMColl_Q9, RRformulas_D2Q9)          */
+} lbm_model;
+
+/* Population storage.  Every storage type holds the shifted populations
+ * g_i = f_i - w_i rho0 (w_i the D2Q9 weights), rounded to nearest-even.  Collision
+ * arithmetic is FP64 for LBM_F64 and FP32 for the others. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 } lbm_storage;
+
+/* Relaxation frequencies per moment order (Sec. 4c): omega_nu for second order
+ * (viscous, trace included), omega3 / omega4 for third / fourth order.  Each must lie in
+ * (0, 2). */
+typedef struct { double omega_nu, omega3, omega4; } lbm_rates;
+
+enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = -1,
+    LBM_ERR_UNSUPPORTED = -2,   /* e.g. periodic = 0: the paper's domains are periodic (Sec. 5a) */
+    LBM_ERR_CUDA = -3,
+    LBM_ERR_BLOWUP = -4,        /* the blow-up criterion fired (see lbm_set_check)               */
+    LBM_ERR_TIMEOUT = -5,       /* a bounded device-side wait gave up                            */
+    LBM_ERR_NOMEM = -6
+};
+
+enum { LBM_PRESET_SRT = 0, LBM_PRESET_REG = 1 };
+
+typedef struct lbm_ctx lbm_ctx;
+typedef struct lbm_group lbm_group;
+
+/* Sec. 4c: omega_nu = 1 / (nu / c_s^2 + 1/2) with c_s^2 = 1/3 (i.e. nu = c_s^2 (tau - 1/2)).
+ * preset LBM_PRESET_SRT: omega3 = omega4 = omega_nu; LBM_PRESET_REG: omega3 = omega4 = 1.
+ * Errors: nu <= 0 or non-finite, unknown preset, out == NULL -> LBM_ERR_INVALID_ARG. */
+int lbm_rates_from_nu(double nu, int preset, lbm_rates* out);
+
+/* Create a periodic nx x ny lattice context.
+ *   periodic  must be 1 (LBM_ERR_UNSUPPORTED otherwise)
+ *   model     lbm_model; storage lbm_storage
+ *   eq_order  4 = extended equilibrium (Eq. extendedFeq, default for every model);
+ *             2 = second-order equilibrium (Sec. 2; Hermite moments of order >= 3 set to
+ *                 zero), accepted for LBM_BGK only (LBM_ERR_UNSUPPORTED otherwise)
+ *   rho0      reference density of the shift g = f - w rho0 (normally 1)
+ * Errors: nx, ny < 3, nx*ny > 2^31, rates outside (0,2), unknown enums -> INVALID_ARG;
+ *         device allocation failure -> LBM_ERR_NOMEM.  *out is NULL on error. */
+int lbm_create(lbm_ctx** out, int nx, int ny, int periodic, int model, lbm_rates rates,
+               int eq_order, int storage, double rho0, void* cuda_stream);
+
+/* Release every device resource of the context (waits for its stream).  NULL is a no-op. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Change the relaxation frequencies used by later steps (same validation as create). */
+int lbm_set_rates(lbm_ctx* ctx, lbm_rates rates);
+
+/* f(x, 0) = f^eq(rho(x), u(x)) (Sec. 5a initial state; Eq. extendedFeq), computed in FP64
+ * and rounded to the storage type; resets the step counter and the blow-up status. */
+int lbm_init_equilibrium(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
+
+/* Advance n >= 0 time steps of Eq. StreamCollide (asynchronous).  Runs the blow-up check of
+ * lbm_set_check at its cadence.  Returns LBM_OK once the work is enqueued; the blow-up
+ * status is read with lbm_status. */
+int lbm_step(lbm_ctx* ctx, long long n);
+
+/* Macroscopic fields of the current pre-collision state f^n: rho = sum f_i,
+ * u = sum xi_i f_i / rho, and the second-order raw moments Pi_ab = sum xi_a xi_b f_i
+ * (Sec. 1; App. B).  Any output pointer may be NULL to skip it. */
+int lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy,
+                double* pxx, double* pxy, double* pyy);
+
+/* FP64 global reductions of the current state (the diagnostics behind the blow-up
+ * criterion of Sec. 5b), out[8] =
+ *   [0] sum rho            [1] sum rho u_x          [2] sum rho u_y
+ *   [3] sum rho |u|^2 / 2  [4] <|u|^2>              [5] <|u - uref|^2>
+ *   [6] min rho            [7] number of nodes with non-finite rho or u
+ * (<.> = mean over nodes; uref set by lbm_set_check).  Per-node values are computed in the
+ * collision precision, sums are accumulated in FP64 in a fixed order (deterministic). */
+int lbm_reduce(lbm_ctx* ctx, double* out8);
+
+/* Canonical pre-collision populations f^n as FP64 [9][ny][nx] (unshifted), and the inverse
+ * (values rounded to the storage type).  Used for checkpoint / resume and tests. */
+int lbm_get_populations(lbm_ctx* ctx, double* f);
+int lbm_set_populations(lbm_ctx* ctx, const double* f);
+
+/* Blow-up check run by lbm_step every `every` steps (0 disables): the state is marked
+ * blown up if any node has a non-finite rho or u, if min rho <= 0, or, when ke_ref > 0,
+ * if <|u|^2> > ke_factor * ke_ref (Sec. 5b: <u^2>/u_0^2 < 1 with ke_ref = u_0^2,
+ * ke_factor = 1).  uref is the reference velocity of out[5] in lbm_reduce. */
+int lbm_set_check(lbm_ctx* ctx, long long every, double ke_ref, double ke_factor,
+                  double uref_x, double uref_y);
+
+/* Wait for the context's stream, then report: *status = LBM_OK or LBM_ERR_BLOWUP,
+ * *blowup_step = first checked step at which the criterion fired (-1 if none),
+ * *steps = steps taken since the last init.  Any pointer may be NULL. */
+int lbm_status(lbm_ctx* ctx, int* status, long long* blowup_step, long long* steps);
+
+/* Wait until all work enqueued on the context's stream has finished. */
+int lbm_synchronize(lbm_ctx* ctx);
+
+/* Grid geometry actually used: row pitch in elements (>= nx, multiple of 32), CUDA grid and
+ * block sizes of the step kernel. */
+int lbm_get_layout(const lbm_ctx* ctx, int* pitch, int* grid, int* block);
+
+/* Several contexts advanced together, one time step of each in turn (so a set of lattices
+ * whose sum exceeds L2 streams from HBM as a single large one would), captured in CUDA
+ * graphs of `graph_steps` steps (even, >= 2; 0 = no graphs).  Every context must use the
+ * same stream.  Blow-up checks of each context run at their own cadence. */
+int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_steps);
+int lbm_group_step(lbm_group* g, long long nsteps);
+void lbm_group_destroy(lbm_group* g);
+/* Optional live timing of the graph replays with CUDA events on the group's stream:
+ * enable, then read the summed duration (ms) of the replays and the number of step-kernel
+ * launches they contained (waits on the stream). */
+int lbm_group_set_timing(lbm_group* g, int enable);
+int lbm_group_timing(lbm_group* g, double* replay_ms, long long* step_launches);
+
+/* Text of the last error on this context (never NULL); lbm_error_string names a code. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+const char* lbm_error_string(int code);
+
+/* Library version string. */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

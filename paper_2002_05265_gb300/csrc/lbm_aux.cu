@@ -1,0 +1,278 @@
+// Auxiliary kernels: equilibrium initialisation, population scatter / gather, moments and
+// the FP64 global reductions behind the blow-up check.  None of these is on the per-step
+// hot path except the reduction, which runs every `check_every` steps.
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kReduceBlocks = 608;   // 4 x 152 SMs; fixed, so the fold order is deterministic
+constexpr int kReduceValues = 8;
+
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// offset of the slot that node (x, y) reads its population i from in a pull step
+__device__ __forceinline__ long long src_offset(int i, int x, int y, const FieldArgs& a) {
+    const int xs = wrap(x - ex_of(i), a.nx), ys = wrap(y - ey_of(i), a.ny);
+    return (long long)i * a.plane + (long long)ys * a.pitch + xs;
+}
+
+template <typename S>
+__global__ void init_eq_kernel(S* buf, FieldArgs a, int eq_order, const double* __restrict__ rho,
+                               const double* __restrict__ ux, const double* __restrict__ uy) {
+    const long long n = (long long)a.nx * a.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+        const double r = rho[k], vx = ux[k], vy = uy[k];
+        const double dr = r - a.rho0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sx = ex_of(i), sy = ey_of(i);
+            double g;
+            if (eq_order == 4) {
+                // Eq. extendedFeq in product form, minus w_i rho0
+                const double Wx = sx ? 1.0 / 6.0 : 2.0 / 3.0, Wy = sy ? 1.0 / 6.0 : 2.0 / 3.0;
+                const double dx = sx ? 0.5 * (vx * vx + sx * vx) : -vx * vx;
+                const double dy = sy ? 0.5 * (vy * vy + sy * vy) : -vy * vy;
+                g = Wx * Wy * dr + r * (Wx * dy + dx * (Wy + dy));
+            } else {
+                const double wi = weight_of(i);
+                const double eu = 3.0 * (sx * vx + sy * vy);
+                g = wi * dr + wi * r * (eu + 0.5 * eu * eu - 1.5 * (vx * vx + vy * vy));
+            }
+            buf[src_offset(i, x, y, a)] = Store<S>::from_double(g);
+        }
+    }
+}
+
+template <typename S>
+__global__ void scatter_kernel(S* buf, FieldArgs a, const double* __restrict__ f) {
+    const long long n = (long long)a.nx * a.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            buf[src_offset(i, x, y, a)] = Store<S>::from_double(f[i * n + k] - weight_of(i) * a.rho0);
+    }
+}
+
+template <typename S>
+__global__ void gather_kernel(const S* buf, FieldArgs a, double* f, double* rho, double* ux, double* uy,
+                              double* pxx, double* pxy, double* pyy) {
+    const long long n = (long long)a.nx * a.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+        double g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = Store<S>::to_double(buf[src_offset(i, x, y, a)]);
+        if (f) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i * n + k] = g[i] + weight_of(i) * a.rho0;
+        }
+        if (rho || ux || uy || pxx || pxy || pyy) {
+            double dr = 0, jx = 0, jy = 0, sxx = 0, sxy = 0, syy = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int sx = ex_of(i), sy = ey_of(i);
+                dr += g[i]; jx += sx * g[i]; jy += sy * g[i];
+                sxx += sx * sx * g[i]; sxy += sx * sy * g[i]; syy += sy * sy * g[i];
+            }
+            const double r = a.rho0 + dr;
+            if (rho) rho[k] = r;
+            if (ux) ux[k] = jx / r;
+            if (uy) uy[k] = jy / r;
+            // sum_i xi_a xi_b w_i = c_s^2 delta_ab
+            if (pxx) pxx[k] = sxx + a.rho0 / 3.0;
+            if (pxy) pxy[k] = sxy;
+            if (pyy) pyy[k] = syy + a.rho0 / 3.0;
+        }
+    }
+}
+
+// Pass 1: per-node rho, u in the collision precision T, accumulated per thread in FP64,
+// then folded per block in a fixed order.  Slots: 0 sum drho, 1 sum rho ux, 2 sum rho uy,
+// 3 sum rho|u|^2/2, 4 sum |u|^2, 5 sum |u-uref|^2, 6 min rho (as drho), 7 non-finite count.
+template <typename S>
+__global__ void __launch_bounds__(kBlock) reduce_kernel(const S* buf, FieldArgs a, double* partials,
+                                                        double urefx, double urefy) {
+    using T = typename Store<S>::T;
+    const long long n = (long long)a.nx * a.ny;
+    double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+        T dr = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const T g = (T)Store<S>::to_double(buf[src_offset(i, x, y, a)]);
+            dr += g;
+            jx += T(ex_of(i)) * g;
+            jy += T(ey_of(i)) * g;
+        }
+        const T r = T(a.rho0) + dr;
+        const T vx = jx / r, vy = jy / r;
+        if (isfinite(r) && isfinite(vx) && isfinite(vy)) {
+            const T u2 = vx * vx + vy * vy;
+            const T wx = vx - T(urefx), wy = vy - T(urefy);
+            acc[0] += (double)dr;
+            acc[1] += (double)jx;
+            acc[2] += (double)jy;
+            acc[3] += 0.5 * (double)(r * u2);
+            acc[4] += (double)u2;
+            acc[5] += (double)(wx * wx + wy * wy);
+            acc[6] = fmin(acc[6], (double)dr);
+        } else {
+            acc[7] += 1.0;
+        }
+    }
+    __shared__ double sh[kBlock / 32][kReduceValues];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < kReduceValues; ++v) {
+        double x = acc[v];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y2 = __shfl_down_sync(0xffffffffu, x, o);
+            x = (v == 6) ? fmin(x, y2) : x + y2;
+        }
+        if (lane == 0) sh[warp][v] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < kReduceValues) {
+        const int v = threadIdx.x;
+        double x = sh[0][v];
+        for (int w = 1; w < kBlock / 32; ++w) x = (v == 6) ? fmin(x, sh[w][v]) : x + sh[w][v];
+        partials[blockIdx.x * kReduceValues + v] = x;
+    }
+}
+
+// Pass 2: one block folds the partials (fixed order), forms the outputs and applies the
+// blow-up criterion.
+__global__ void __launch_bounds__(kBlock) reduce_finish_kernel(const double* partials, int nparts, FieldArgs a,
+                                                               double* out, int* status, long long* blowup_step,
+                                                               CheckArgs c) {
+    __shared__ double sh[kBlock][kReduceValues];
+    double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+#pragma unroll
+        for (int v = 0; v < kReduceValues; ++v) {
+            const double x = partials[b * kReduceValues + v];
+            acc[v] = (v == 6) ? fmin(acc[v], x) : acc[v] + x;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kReduceValues; ++v) sh[threadIdx.x][v] = acc[v];
+    __syncthreads();
+    for (int s = kBlock / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+#pragma unroll
+            for (int v = 0; v < kReduceValues; ++v)
+                sh[threadIdx.x][v] = (v == 6) ? fmin(sh[threadIdx.x][v], sh[threadIdx.x + s][v])
+                                              : sh[threadIdx.x][v] + sh[threadIdx.x + s][v];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double n = (double)a.nx * (double)a.ny;
+        const double* t = sh[0];
+        double o[kReduceValues];
+        o[0] = n * a.rho0 + t[0];
+        o[1] = t[1];
+        o[2] = t[2];
+        o[3] = t[3];
+        o[4] = t[4] / n;
+        o[5] = t[5] / n;
+        o[6] = a.rho0 + t[6];
+        o[7] = t[7];
+        for (int v = 0; v < kReduceValues; ++v) out[v] = o[v];
+        if (c.apply && status && *status == 0) {
+            const bool blown = (o[7] > 0.0) || !(o[6] > 0.0) ||
+                               (c.ke_ref > 0.0 && o[4] > c.ke_factor * c.ke_ref);
+            if (blown) {
+                *status = -4;   // LBM_ERR_BLOWUP
+                *blowup_step = c.step;
+            }
+        }
+    }
+}
+
+int grid_for(long long n) {
+    long long g = (n + kBlock - 1) / kBlock;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename S>
+cudaError_t init_t(void* buf, const FieldArgs& a, int eq, const double* r, const double* x, const double* y, cudaStream_t s) {
+    init_eq_kernel<S><<<grid_for((long long)a.nx * a.ny), kBlock, 0, s>>>((S*)buf, a, eq, r, x, y);
+    return cudaGetLastError();
+}
+template <typename S>
+cudaError_t scatter_t(void* buf, const FieldArgs& a, const double* f, cudaStream_t s) {
+    scatter_kernel<S><<<grid_for((long long)a.nx * a.ny), kBlock, 0, s>>>((S*)buf, a, f);
+    return cudaGetLastError();
+}
+template <typename S>
+cudaError_t gather_t(const void* buf, const FieldArgs& a, double* f, double* r, double* x, double* y,
+                     double* pxx, double* pxy, double* pyy, cudaStream_t s) {
+    gather_kernel<S><<<grid_for((long long)a.nx * a.ny), kBlock, 0, s>>>((const S*)buf, a, f, r, x, y, pxx, pxy, pyy);
+    return cudaGetLastError();
+}
+template <typename S>
+cudaError_t reduce_t(const void* buf, const FieldArgs& a, double* partials, double* out8, int* status,
+                     long long* blowup_step, const CheckArgs& c, cudaStream_t s) {
+    reduce_kernel<S><<<kReduceBlocks, kBlock, 0, s>>>((const S*)buf, a, partials, c.uref_x, c.uref_y);
+    reduce_finish_kernel<<<1, kBlock, 0, s>>>(partials, kReduceBlocks, a, out8, status, blowup_step, c);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int reduce_blocks() { return kReduceBlocks; }
+
+#define LBM_DISPATCH(storage, call)                                     \
+    switch (storage) {                                                  \
+        case 0: { using S = double; return call; }                      \
+        case 1: { using S = float; return call; }                       \
+        case 2: { using S = __half; return call; }                      \
+        case 3: { using S = __nv_bfloat16; return call; }               \
+        default: return cudaErrorInvalidValue;                          \
+    }
+
+cudaError_t launch_init_eq(int storage, void* buf, const FieldArgs& a, int eq_order,
+                           const double* rho, const double* ux, const double* uy, cudaStream_t s) {
+    LBM_DISPATCH(storage, init_t<S>(buf, a, eq_order, rho, ux, uy, s));
+}
+cudaError_t launch_scatter(int storage, void* buf, const FieldArgs& a, const double* f, cudaStream_t s) {
+    LBM_DISPATCH(storage, scatter_t<S>(buf, a, f, s));
+}
+cudaError_t launch_gather(int storage, const void* buf, const FieldArgs& a, double* f, double* rho, double* ux,
+                          double* uy, double* pxx, double* pxy, double* pyy, cudaStream_t s) {
+    LBM_DISPATCH(storage, gather_t<S>(buf, a, f, rho, ux, uy, pxx, pxy, pyy, s));
+}
+cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, double* partials, double* out8,
+                          int* status, long long* blowup_step, const CheckArgs& c, cudaStream_t s) {
+    LBM_DISPATCH(storage, reduce_t<S>(buf, a, partials, out8, status, blowup_step, c, s));
+}
+
+int storage_vec(int storage) {
+    switch (storage) {
+        case 0: return Store<double>::VEC;
+        case 1: return Store<float>::VEC;
+        case 2: return Store<__half>::VEC;
+        case 3: return Store<__nv_bfloat16>::VEC;
+        default: return 0;
+    }
+}
+int storage_bytes(int storage) {
+    switch (storage) {
+        case 0: return 8;
+        case 1: return 4;
+        case 2: case 3: return 2;
+        default: return 0;
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,272 @@
+"""ctypes binding of liblbm.so (C ABI in include/lbm.h).  Argument marshalling only: every
+step of the method runs in the CUDA library.  If the library is missing or cannot be loaded
+the calls raise; there is no fallback.
+
+Field arguments may be torch tensors (CUDA or CPU, float64, contiguous), numpy float64
+arrays, or raw integer addresses.  Streams may be a torch.cuda.Stream, an int handle or None
+(legacy default stream).
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_BGK, LBM_RM, LBM_HM, LBM_CM, LBM_CHM, LBM_K, LBM_PR, LBM_RR = range(8)
+LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = range(4)
+LBM_PRESET_SRT, LBM_PRESET_REG = 0, 1
+LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_CUDA, LBM_ERR_BLOWUP, LBM_ERR_TIMEOUT, LBM_ERR_NOMEM = \
+    0, -1, -2, -3, -4, -5, -6
+
+MODELS = {"bgk": LBM_BGK, "rm": LBM_RM, "hm": LBM_HM, "cm": LBM_CM, "chm": LBM_CHM, "k": LBM_K,
+          "pr": LBM_PR, "rr": LBM_RR}
+STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
+STORAGE_BYTES = {LBM_F64: 8, LBM_F32: 4, LBM_F16: 2, LBM_BF16: 2}
+
+
+class lbm_rates(ctypes.Structure):
+    _fields_ = [("omega_nu", ctypes.c_double), ("omega3", ctypes.c_double), ("omega4", ctypes.c_double)]
+
+    def as_tuple(self):
+        return (self.omega_nu, self.omega3, self.omega4)
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"liblbm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_LL = ctypes.c_longlong
+_D = ctypes.c_double
+
+_SIGNATURES = {
+    "lbm_rates_from_nu": (_I, [_D, _I, ctypes.POINTER(lbm_rates)]),
+    "lbm_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, lbm_rates, _I, _I, _D, _P]),
+    "lbm_destroy": (None, [_P]),
+    "lbm_set_rates": (_I, [_P, lbm_rates]),
+    "lbm_init_equilibrium": (_I, [_P, _P, _P, _P]),
+    "lbm_step": (_I, [_P, _LL]),
+    "lbm_moments": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "lbm_reduce": (_I, [_P, _P]),
+    "lbm_get_populations": (_I, [_P, _P]),
+    "lbm_set_populations": (_I, [_P, _P]),
+    "lbm_set_check": (_I, [_P, _LL, _D, _D, _D, _D]),
+    "lbm_status": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
+    "lbm_synchronize": (_I, [_P]),
+    "lbm_get_layout": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "lbm_group_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _I]),
+    "lbm_group_step": (_I, [_P, _LL]),
+    "lbm_group_destroy": (None, [_P]),
+    "lbm_group_set_timing": (_I, [_P, _I]),
+    "lbm_group_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_LL)]),
+    "lbm_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_error_string": (ctypes.c_char_p, [_I]),
+    "lbm_version": (ctypes.c_char_p, []),
+}
+
+
+def load_library(path=LIB_PATH):
+    """Load liblbm.so (raises if it is absent: build it with paper_2002_05265_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing; build it with `python -m paper_2002_05265_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _addr(x):
+    """Address of a field argument (torch tensor, numpy array, int or None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("fields must be contiguous float64 tensors")
+        return x.data_ptr()
+    if hasattr(x, "__array_interface__"):
+        import numpy as np
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("fields must be C-contiguous float64 arrays")
+        return x.__array_interface__["data"][0]
+    raise TypeError(f"unsupported field argument {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc, ctx=None):
+    if rc != LBM_OK:
+        lib = load_library()
+        msg = lib.lbm_last_error(ctx).decode() if ctx else lib.lbm_error_string(rc).decode()
+        raise LBMError(rc, msg or lib.lbm_error_string(rc).decode())
+
+
+def lbm_rates_from_nu(nu, preset=LBM_PRESET_SRT):
+    r = lbm_rates()
+    _check(load_library().lbm_rates_from_nu(nu, preset, ctypes.byref(r)))
+    return r
+
+
+def lbm_create(nx, ny, model, rates, storage=LBM_F32, eq_order=4, rho0=1.0, stream=None, periodic=1):
+    if isinstance(model, str):
+        model = MODELS[model]
+    if isinstance(storage, str):
+        storage = STORAGES[storage]
+    if not isinstance(rates, lbm_rates):
+        rates = lbm_rates(*rates)
+    h = _P()
+    _check(load_library().lbm_create(ctypes.byref(h), nx, ny, periodic, model, rates, eq_order, storage, rho0,
+                                     _stream(stream)))
+    return h.value
+
+
+def lbm_destroy(ctx):
+    load_library().lbm_destroy(ctx)
+
+
+def lbm_set_rates(ctx, rates):
+    if not isinstance(rates, lbm_rates):
+        rates = lbm_rates(*rates)
+    _check(load_library().lbm_set_rates(ctx, rates), ctx)
+
+
+def lbm_init_equilibrium(ctx, rho, ux, uy):
+    _check(load_library().lbm_init_equilibrium(ctx, _addr(rho), _addr(ux), _addr(uy)), ctx)
+
+
+def lbm_step(ctx, n):
+    _check(load_library().lbm_step(ctx, n), ctx)
+
+
+def lbm_moments(ctx, rho=None, ux=None, uy=None, pxx=None, pxy=None, pyy=None):
+    _check(load_library().lbm_moments(ctx, _addr(rho), _addr(ux), _addr(uy), _addr(pxx), _addr(pxy), _addr(pyy)), ctx)
+
+
+def lbm_reduce(ctx, out8):
+    _check(load_library().lbm_reduce(ctx, _addr(out8)), ctx)
+
+
+def lbm_get_populations(ctx, f):
+    _check(load_library().lbm_get_populations(ctx, _addr(f)), ctx)
+
+
+def lbm_set_populations(ctx, f):
+    _check(load_library().lbm_set_populations(ctx, _addr(f)), ctx)
+
+
+def lbm_set_check(ctx, every, ke_ref=0.0, ke_factor=1.0, uref=(0.0, 0.0)):
+    _check(load_library().lbm_set_check(ctx, every, ke_ref, ke_factor, uref[0], uref[1]), ctx)
+
+
+def lbm_status(ctx):
+    st, bs, n = _I(), _LL(), _LL()
+    _check(load_library().lbm_status(ctx, ctypes.byref(st), ctypes.byref(bs), ctypes.byref(n)), ctx)
+    return st.value, bs.value, n.value
+
+
+def lbm_synchronize(ctx):
+    _check(load_library().lbm_synchronize(ctx), ctx)
+
+
+def lbm_get_layout(ctx):
+    p, g, b = _I(), _I(), _I()
+    _check(load_library().lbm_get_layout(ctx, ctypes.byref(p), ctypes.byref(g), ctypes.byref(b)), ctx)
+    return p.value, g.value, b.value
+
+
+def lbm_group_create(ctxs, graph_steps=64):
+    arr = (_P * len(ctxs))(*ctxs)
+    h = _P()
+    _check(load_library().lbm_group_create(ctypes.byref(h), arr, len(ctxs), graph_steps), ctxs[0])
+    return h.value
+
+
+def lbm_group_step(group, n, ctx_for_errors=None):
+    _check(load_library().lbm_group_step(group, n), ctx_for_errors)
+
+
+def lbm_group_destroy(group):
+    load_library().lbm_group_destroy(group)
+
+
+def lbm_group_set_timing(group, enable=True):
+    _check(load_library().lbm_group_set_timing(group, 1 if enable else 0))
+
+
+def lbm_group_timing(group):
+    ms, n = _D(), _LL()
+    _check(load_library().lbm_group_timing(group, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def lbm_version():
+    return load_library().lbm_version().decode()
+
+
+class Lattice:
+    """Owns one lbm_ctx; methods forward to the C calls of the same names."""
+
+    def __init__(self, nx, ny, model, rates, storage=LBM_F32, eq_order=4, rho0=1.0, stream=None):
+        self.nx, self.ny = nx, ny
+        self.ctx = lbm_create(nx, ny, model, rates, storage, eq_order, rho0, stream)
+
+    def close(self):
+        if self.ctx:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_equilibrium(self, rho, ux, uy):
+        lbm_init_equilibrium(self.ctx, rho, ux, uy)
+
+    def step(self, n):
+        lbm_step(self.ctx, n)
+
+    def moments(self, *fields):
+        lbm_moments(self.ctx, *fields)
+
+    def reduce(self, out8):
+        lbm_reduce(self.ctx, out8)
+
+    def get_populations(self, f):
+        lbm_get_populations(self.ctx, f)
+
+    def set_populations(self, f):
+        lbm_set_populations(self.ctx, f)
+
+    def set_check(self, every, ke_ref=0.0, ke_factor=1.0, uref=(0.0, 0.0)):
+        lbm_set_check(self.ctx, every, ke_ref, ke_factor, uref)
+
+    def status(self):
+        return lbm_status(self.ctx)
+
+    def synchronize(self):
+        lbm_synchronize(self.ctx)
+
+    def set_rates(self, rates):
+        lbm_set_rates(self.ctx, rates)
