@@ -119,6 +119,40 @@ int lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy,
  * collision precision, sums are accumulated in FP64 in a fixed order (deterministic). */
 int lbm_reduce(lbm_ctx* ctx, double* out8);
 
+/* lbm_reduce without any allocation, for a population buffer the caller owns.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot allocate device
+ * memory when they need the diagnostics -- code that runs while another component is
+ * capturing a CUDA graph in global mode (cudaMalloc is illegal there), code whose device
+ * memory is owned entirely by a pool or caching allocator of the host application, and
+ * latency-bound loops that must not call cudaMalloc/cudaFree (they synchronise the device).
+ * lbm_reduce itself is unsuitable for them because lbm_create allocates.
+ *
+ *   populations  device pointer to one population buffer in the library's layout: nine
+ *                planes g_i[y][x] (i in the index order above), row pitch `pitch` elements,
+ *                plane = ny * pitch elements, element type given by `storage`, holding
+ *                g_i = f_i - w_i rho0 with node x's population i at plane i, position
+ *                x - xi_i (periodic), i.e. the state that the next pull step would read
+ *   nx, ny       lattice size, 3 <= nx <= pitch, ny >= 3, nx * ny <= 2^31 (larger lattices
+ *                are rejected with LBM_ERR_INVALID_ARG)
+ *   uref_x/_y    reference velocity of out[5]
+ *   out8         device pointer to 8 doubles, same meaning as lbm_reduce (host pointers are
+ *                rejected: copying them back would need staging memory)
+ *   cuda_stream  stream to run on (NULL = legacy default stream); asynchronous
+ * Returns LBM_ERR_INVALID_ARG for a null, misaligned or non-device pointer, an unknown
+ * storage or out-of-range sizes, LBM_ERR_CUDA if a launch fails.
+ *
+ * Scratch: the per-block partial sums go to one file-scope device array of 608 x 8 doubles
+ * (38,912 bytes), which every GPU that loads the library holds until the process exits.  The
+ * first call on each device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture that could contain it.
+ * All calls share the array: calls that overlap on the GPU (e.g. on two streams at once)
+ * race and give wrong results.  Each call rewrites every partial before reading it, so no
+ * call depends on what the previous one left there.  No cudaMalloc, cudaFree or other
+ * allocating routine is called. */
+int lbm_reduce_noalloc(const void* populations, int storage, int nx, int ny, int pitch, double rho0,
+                       double uref_x, double uref_y, double* out8, void* cuda_stream);
+
 /* Canonical pre-collision populations f^n as FP64 [9][ny][nx] (unshifted), and the inverse
  * (values rounded to the storage type).  Used for checkpoint / resume and tests. */
 int lbm_get_populations(lbm_ctx* ctx, double* f);

@@ -1,6 +1,12 @@
 // Auxiliary kernels: equilibrium initialisation, population scatter / gather, moments and
 // the FP64 global reductions behind the blow-up check.  None of these is on the per-step
 // hot path except the reduction, which runs every `check_every` steps.
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "lbm.h"
+
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -276,3 +282,73 @@ int storage_bytes(int storage) {
 }
 
 }  // namespace lbm
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free reductions (lbm_reduce_noalloc in include/lbm.h).
+//
+// The two reduction passes above need a scratch array for the per-block partial sums.  For
+// callers that cannot allocate device memory, that scratch lives in this file-scope device
+// array instead: 608 blocks x 8 doubles = 38,912 bytes, allocated by the CUDA runtime when
+// the library's module loads on a device and held by every device that loads it until the
+// process exits.  Its host-side name is not a device address: host code obtains the device
+// address once per device with cudaGetSymbolAddress, while that device is current, and passes
+// that address to the kernels.
+namespace lbm {
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_partials[kReduceBlocks * kReduceValues];
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+bool noalloc_is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+}  // namespace
+
+}  // namespace lbm
+
+extern "C" int lbm_reduce_noalloc(const void* populations, int storage, int nx, int ny, int pitch, double rho0,
+                                  double uref_x, double uref_y, double* out8, void* cuda_stream) {
+    using namespace lbm;
+    if (!populations || !out8) return LBM_ERR_INVALID_ARG;
+    if (storage < LBM_F64 || storage > LBM_BF16) return LBM_ERR_INVALID_ARG;
+    if (nx < 3 || ny < 3 || pitch < nx) return LBM_ERR_INVALID_ARG;
+    // the largest lattice accepted: 2^31 nodes, as for lbm_create
+    if ((long long)nx * (long long)ny > (1LL << 31)) return LBM_ERR_INVALID_ARG;
+    if (!(rho0 > 0.0) || !std::isfinite(rho0) || !std::isfinite(uref_x) || !std::isfinite(uref_y))
+        return LBM_ERR_INVALID_ARG;
+    const size_t esize = (size_t)storage_bytes(storage);
+    if (((uintptr_t)populations % esize) != 0 || ((uintptr_t)out8 % sizeof(double)) != 0) return LBM_ERR_INVALID_ARG;
+    if (!noalloc_is_device_ptr(populations) || !noalloc_is_device_ptr(out8)) return LBM_ERR_INVALID_ARG;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return LBM_ERR_CUDA;
+    double* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return LBM_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = static_cast<double*>(p);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    FieldArgs a;
+    a.nx = nx; a.ny = ny; a.pitch = pitch; a.plane = (long long)ny * pitch; a.rho0 = rho0;
+    CheckArgs c;
+    c.ke_ref = 0.0; c.ke_factor = 1.0; c.uref_x = uref_x; c.uref_y = uref_y; c.step = 0; c.apply = 0;
+    // pass 1 overwrites every partial slot before pass 2 reads it (same stream), so nothing in
+    // the shared array needs clearing between calls
+    cudaError_t e = launch_reduce(storage, populations, a, scratch, out8, nullptr, nullptr, c,
+                                  (cudaStream_t)cuda_stream);
+    return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
