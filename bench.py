@@ -51,7 +51,17 @@ def parse():
     p.add_argument("--sim-steps", type=int, default=SIM_STEPS)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--per-model", action="store_true", help="also time each model alone on 4096^2")
+    p.add_argument("--no-per-model", action="store_true", help="skip the per-model 4096^2 timing")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint / forward time ratio")
+    p.add_argument("--batch", action="store_true",
+                   help="instead of the benchmark step, run the batched stability sweep (4096 lattices)")
+    p.add_argument("--instances", type=int, default=4096)
+    p.add_argument("--batch-steps", type=int, default=50000)
+    p.add_argument("--accuracy", type=int, default=0,
+                   help="instead of the benchmark step, the storage-accuracy study on an LxL vortex (L given)")
+    p.add_argument("--sweep", default=None,
+                   help="instead of the benchmark step, time single lattices: MODELS:STORAGES:SIZE, e.g. "
+                        "all:f32,f16,bf16:16384 (one JSON line per combination)")
     return p.parse_args()
 
 
@@ -183,6 +193,40 @@ def cpu_baseline(n_models=len(MODELS)):
                       f"({lu} lattice updates, {dt:.1f} s), numpy FP64 single-threaded"}
 
 
+def adjoint_ratio(lbm, flows, stream):
+    """Adjoint / forward time ratio on the 512 x 512 vortex, 4000 steps, FP32, REG rates,
+    misfit loss, sqrt(N) checkpoints: backward (recomputation + adjoint steps) over the plain
+    forward run of the same 4000 steps."""
+    import torch
+    N, n = 512, 4000
+    u0 = 0.1 / np.sqrt(3.0)
+    rho, ux, uy = flows.vortex(N, Ma=0.1)
+    _, tx, ty = flows.vortex(N, Ma=0.1, center=((N / 2 + u0 * n) % N, N / 2))
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (rho, ux, uy, tx, ty)]
+    w = 1.0 / (3e-4 + 0.5)
+    res = {}
+    for m in ("chm", "k"):
+        lat = lbm.Lattice(N, N, lbm.MODELS[m], (w, 1.0, 1.0), storage=lbm.LBM_F32, stream=stream)
+        lat.init_equilibrium(*dev[:3])
+        lat.step(64)
+        lat.synchronize()
+        lat.init_equilibrium(*dev[:3])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(n)
+        e1.record(stream)
+        stream.synchronize()
+        fwd = e0.elapsed_time(e1)
+        lat.init_equilibrium(*dev[:3])
+        gx = torch.empty_like(dev[1])
+        gy = torch.empty_like(dev[2])
+        loss, gr, (f_ms, b_ms) = lbm.lbm_adjoint_run(lat.ctx, n, 0, dev[3], dev[4], gx, gy, 0)
+        lat.close()
+        res[m] = {"forward_ms": fwd, "forward_with_checkpoints_ms": f_ms, "backward_ms": b_ms,
+                  "ratio": b_ms / fwd, "loss": loss}
+    return {"workload": "512x512 vortex, 4000 steps, FP32, REG rates, misfit loss, 64 checkpoints", "models": res}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -215,11 +259,190 @@ def run_reference(args, rank, world):
     print(json.dumps(out))
 
 
+def run_accuracy(args):
+    """Error of reduced-precision storage after 10 domain traversals of the convected vortex
+    (Ma = 0.2, radius 0.1 L, L x L, no seed noise, so that nothing but the storage differs):
+    normalised L2 velocity error of every model with FP32, FP16 and BF16 storage (shift
+    w rho0, and shift at the mean flow) against the FP64 kernel on the same lattice (itself
+    checked against the FP64 CPU oracle by the tests).  nu = 1e-6 (the high-Reynolds case,
+    where several models blow up, as in the paper's stability maps) and nu = 1e-4 (stable for
+    every model).  One JSON line per nu x model x storage."""
+    import torch
+    from paper_2002_05265_gb300 import build, flows, lbm
+    build.build_library()
+    lbm.load_library()
+    n = args.accuracy
+    Ma = 0.2
+    u0 = Ma / np.sqrt(3.0)
+    steps = int(round(10 * n / u0))
+    fields = [torch.from_numpy(a).cuda() for a in flows.vortex(n, Ma=Ma)]
+
+    def velocity(model, storage, shift, w):
+        rates = (w, w, w) if _preset(model) == "srt" else (w, 1.0, 1.0)
+        lat = lbm.Lattice(n, n, lbm.MODELS[model], rates, storage=lbm.STORAGES[storage])
+        if shift:
+            lat.set_shift_velocity(u0, 0.0)
+        lat.init_equilibrium(*fields)
+        lat.step(steps)
+        ux = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        uy = torch.empty_like(ux)
+        lat.moments(None, ux, uy)
+        lat.close()
+        return ux, uy
+
+    for nu in (1e-6, 1e-4):
+        w = 1.0 / (3.0 * nu + 0.5)
+        for m in MODELS:
+            rx, ry = velocity(m, "f64", False, w)
+            ok = bool(torch.isfinite(rx).all() and torch.isfinite(ry).all())
+            norm = torch.sqrt((rx * rx + ry * ry).sum())
+            for storage, shift in (("f32", False), ("f16", False), ("bf16", False), ("f16", True), ("bf16", True)):
+                gx, gy = velocity(m, storage, shift, w)
+                err = float(torch.sqrt(((gx - rx) ** 2 + (gy - ry) ** 2).sum()) / norm) if ok else None
+                print(json.dumps({"accuracy": True, "nu": nu, "model": m, "storage": storage,
+                                  "shift": "mean flow" if shift else "w rho0", "lattice": f"{n}x{n}",
+                                  "steps": steps, "traversals": 10, "fp64_reference_finite": ok,
+                                  "l2_rel_error_u": err, "finite": bool(torch.isfinite(gx).all())}), flush=True)
+
+
+def run_sweep(args):
+    """Single-lattice throughput per model x storage on the convected vortex (Ma = 0.2,
+    nu = 1e-6): `--steps` timed time steps after `--warmup`, CUDA events around the graph
+    replays of the step kernel only."""
+    import torch
+    from paper_2002_05265_gb300 import build, flows, lbm
+    build.build_library()
+    lbm.load_library()
+    ms, st, size = args.sweep.split(":")
+    models = MODELS if ms == "all" else ms.split(",")
+    storages = st.split(",")
+    n = int(size)
+    stream = torch.cuda.Stream()
+    fields = [torch.from_numpy(a).cuda() for a in flows.vortex(n, Ma=0.2, noise=1e-8, seed=3)]
+    for s in storages:
+        for m in models:
+            rates = lbm.lbm_rates_from_nu(1e-6, lbm.LBM_PRESET_SRT if _preset(m) == "srt" else lbm.LBM_PRESET_REG)
+            lat = lbm.Lattice(n, n, lbm.MODELS[m], rates, storage=lbm.STORAGES[s], stream=stream)
+            lat.init_equilibrium(*fields)
+            g = lbm.lbm_group_create([lat.ctx], graph_steps=2)
+            lbm.lbm_group_step(g, max(2, args.warmup - args.warmup % 2), lat.ctx)
+            lbm.lbm_group_set_timing(g, True)
+            lbm.lbm_group_step(g, args.steps - args.steps % 2, lat.ctx)
+            rms, nl, _ = lbm.lbm_group_timing(g)
+            t = rms / 1e3 / nl
+            print(json.dumps({"sweep": True, "model": m, "storage": s, "lattice": f"{n}x{n}", "steps": nl,
+                              "glups": n * n / t / 1e9, "gbs": BYTES_PER_LU[s] * n * n / t / 1e9,
+                              "ms_per_step": t * 1e3}), flush=True)
+            lbm.lbm_group_destroy(g)
+            lat.close()
+            torch.cuda.synchronize()
+
+
+def shard(items, rank, world):
+    """Instances of the batched sweep owned by one rank: every world-th instance (the
+    instances are independent, so ranks share nothing but the final timing reduction)."""
+    return items[rank::world]
+
+
+def batch_workload(n, seed=4):
+    """The batched stability sweep: n lattices, nx, ny ~ U{32..256} independently, model
+    uniform over the 8 models, preset uniform over SRT/REG, Ma ~ U[0, 0.6] along +x,
+    nu log-uniform in [1e-7, 1e-2], rho = 1, u = (Ma c_s, 0) + U(-1e-6, 1e-6) noise."""
+    from paper_2002_05265_gb300 import flows
+    g = np.random.Generator(np.random.Philox(seed))
+    descs, fields = [], []
+    cs = 1.0 / np.sqrt(3.0)
+    for k in range(n):
+        nx, ny = (int(v) for v in g.integers(32, 257, 2))
+        m = MODELS[int(g.integers(0, len(MODELS)))]
+        preset = "srt" if g.integers(0, 2) == 0 else "reg"
+        Ma = float(g.uniform(0.0, 0.6))
+        nu = float(np.exp(g.uniform(np.log(1e-7), np.log(1e-2))))
+        w = 1.0 / (nu * 3.0 + 0.5)
+        rates = (w, w, w) if preset == "srt" else (w, 1.0, 1.0)
+        descs.append(dict(nx=nx, ny=ny, model=m, preset=preset, Ma=Ma, nu=nu, rates=rates,
+                          ux_ref=Ma * cs, uy_ref=0.0))
+        fields.append(flows.uniform_noise(nx, ny, Ma=Ma, amp=1e-6, seed=10000 + k))
+    return descs, fields
+
+
+def run_batch(args, rank=0, world=1):
+    """Batched stability sweep throughput (one persistent launch in a CUDA graph) against
+    the plain per-lattice FP32 kernel on a 256-instance subset.  With several ranks the
+    instances are sharded (weak scaling, no collective but the timing maximum)."""
+    import torch
+    from paper_2002_05265_gb300 import build, lbm
+    build.build_library()
+    lbm.load_library()
+    descs, fields = batch_workload(args.instances)
+    descs, fields = shard(descs, rank, world), shard(fields, rank, world)
+    stream = torch.cuda.Stream()
+    b = lbm.lbm_batch_create(descs, storage=lbm.LBM_F32, stream=stream)
+    cat = [torch.from_numpy(np.ascontiguousarray(np.concatenate([f[i].ravel() for f in fields]))).cuda()
+           for i in range(3)]
+    nodes = lbm.lbm_batch_nodes(b)
+    lbm.lbm_batch_init_equilibrium(b, *cat)
+    vec, block, trial_ms = lbm.lbm_batch_autotune(b, trial_steps=200, check_every=CHECK_EVERY)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        lbm.lbm_batch_run(b, args.batch_steps, check_every=CHECK_EVERY, growth=1e4)
+        ev1.record(stream)
+        stream.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st, bs, steps, diag = lbm.lbm_batch_status(b, len(descs))
+    lu = float(sum(int(s) * d["nx"] * d["ny"] for s, d in zip(steps, descs)))
+    stable = {}
+    for d, s in zip(descs, st):
+        key = f'{d["preset"]}-{d["model"]}'
+        a = stable.setdefault(key, [0, 0])
+        a[0] += int(s == 0)
+        a[1] += 1
+    # plain per-lattice kernel: 256 instances, one context each, 1000 steps each
+    sub = list(range(0, len(descs), max(1, len(descs) // 256)))[:256]
+    lu_sub, t_sub = 0.0, 0.0
+    with torch.cuda.stream(stream):
+        for k in sub:
+            d = descs[k]
+            lat = lbm.Lattice(d["nx"], d["ny"], lbm.MODELS[d["model"]], d["rates"], storage=lbm.LBM_F32, stream=stream)
+            lat.set_shift_velocity(d["ux_ref"], 0.0)
+            lat.init_equilibrium(*[torch.from_numpy(a).cuda() for a in fields[k]])
+            lat.step(64)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(1000)
+            e1.record(stream)
+            stream.synchronize()
+            t_sub += e0.elapsed_time(e1) / 1e3
+            lu_sub += 1000.0 * d["nx"] * d["ny"]
+            lat.close()
+    lbm.lbm_batch_destroy(b)
+    print(json.dumps({
+        "batch": True, "metric": "batched stability sweep, lattice updates per second", "unit": "GLUPS",
+        "value": lu / (ms / 1e3) / 1e9, "instances": len(descs), "nodes": nodes, "target_steps": args.batch_steps,
+        "lattice_updates": lu, "ms": ms, "shape": {"vec": vec, "block": block, "trial_ms": trial_ms},
+        "stable_instances": int((st == 0).sum()), "blown_up": int((st != 0).sum()),
+        "stable_by_model": {k: f"{v[0]}/{v[1]}" for k, v in sorted(stable.items())},
+        "per_instance_kernel_glups": lu_sub / t_sub / 1e9,
+        "per_instance_subset": f"{len(sub)} instances x 1000 steps, one context and graph each",
+        "dtype": "f32", "data": "synthetic"}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.sweep:
+        run_sweep(args)
+        return
+    if args.batch:
+        run_batch(args, rank, world)
+        return
+    if args.accuracy:
+        run_accuracy(args)
         return
     import torch
     from paper_2002_05265_gb300 import build, flows, lbm
@@ -273,7 +496,7 @@ def main():
         barrier(world)
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
-        replay_ms, step_launches = lbm.lbm_group_timing(group)
+        replay_ms, lattice_steps, kernel_launches = lbm.lbm_group_timing(group)
         lbm.lbm_group_set_timing(group, False)
     ms = max_over_ranks(ms, world)
     statuses = {m: lat.status()[:2] for m, lat in zip(MODELS, lats)}
@@ -281,17 +504,21 @@ def main():
     lu_per_step = len(MODELS) * L * L * S
     value = world * lu_per_step * args.steps / (ms / 1e3) / 1e9
 
-    # dominant kernel: the fused step kernel (all models); average launch duration from the
-    # CUDA events around every graph replay of the timed region
+    # dominant kernel: the multi-lattice step kernel (one launch advances the 8 lattices one
+    # time step); average launch duration from the CUDA events around every graph replay of
+    # the timed region (the graphs contain only step launches)
     peak, peak_kind = measured_peaks()
-    avg_launch_s = replay_ms / 1e3 / step_launches
-    achieved = BYTES_PER_LU["f32"] * L * L / avg_launch_s / 1e9
-    traffic = ncu_traffic("f32_1024")
+    avg_launch_s = replay_ms / 1e3 / kernel_launches
+    bytes_per_launch = BYTES_PER_LU["f32"] * L * L * lattice_steps / kernel_launches
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    traffic = ncu_traffic("f32_group_8x1024")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "lbm::step_kernel<model, 4, float> (8 models), 72 B per lattice update"}
+                "traffic": traffic, "peak_source": peak_kind, "launch_us": avg_launch_s * 1e6,
+                "bytes_per_launch": bytes_per_launch,
+                "kernel": "lbm::group_step_kernel<float>: one launch = one time step of the 8 lattices, "
+                          "72 B per lattice update"}
 
-    launches_per_step = len(MODELS) * (1 + S + 2 * (S // CHECK_EVERY) + 1)
+    launches_per_step = S + len(MODELS) * (1 + 2 * (S // CHECK_EVERY) + 1)
 
     e2e = None
     if not args.no_e2e:
@@ -310,7 +537,7 @@ def main():
                "d2h_bytes_per_step": len(MODELS) * 3 * L * L * 8}
 
     per_model = None
-    if args.per_model:
+    if not args.no_per_model:
         per_model = {}
         for m in MODELS:
             rates = lbm.lbm_rates_from_nu(NU, lbm.LBM_PRESET_SRT if _preset(m) == "srt" else lbm.LBM_PRESET_REG)
@@ -321,11 +548,16 @@ def main():
             lbm.lbm_group_step(g1, 64, big.ctx)
             lbm.lbm_group_set_timing(g1, True)
             lbm.lbm_group_step(g1, 256, big.ctx)
-            rms, nl = lbm.lbm_group_timing(g1)
+            rms, nl, _ = lbm.lbm_group_timing(g1)
             t = rms / 1e3 / nl
-            per_model[m] = {"glups": 4096 * 4096 / t / 1e9, "gbs": 72 * 4096 * 4096 / t / 1e9}
+            per_model[m] = {"glups": 4096 * 4096 / t / 1e9, "gbs": 72 * 4096 * 4096 / t / 1e9,
+                            "frac": 72 * 4096 * 4096 / t / 1e9 / peak}
             lbm.lbm_group_destroy(g1)
             big.close()
+
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_ratio(lbm, flows, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -347,6 +579,8 @@ def main():
                "blowup": {m: (s[1] if s[0] != 0 else None) for m, s in statuses.items()}}
         if per_model:
             out["per_model_4096_f32"] = per_model
+        if adjoint:
+            out["adjoint"] = adjoint
         print(json.dumps(out))
 
     lbm.lbm_group_destroy(group)

@@ -95,6 +95,14 @@ void lbm_destroy(lbm_ctx* ctx);
 /* Change the relaxation frequencies used by later steps (same validation as create). */
 int lbm_set_rates(lbm_ctx* ctx, lbm_rates rates);
 
+/* Change the storage shift to s_i = f^eq_i(rho0, u_ref) (extended equilibrium at a reference
+ * velocity; the default u_ref = 0 gives s_i = w_i rho0) and re-encode the current state.
+ * Choosing u_ref near the flow's mean velocity keeps the stored deviations small, which
+ * cuts the rounding error of FP16/BF16 storage.  Not a concept of the paper: a storage
+ * detail.  Errors: non-finite or |u_ref| >= 1 -> INVALID_ARG; eq_order = 2 with u_ref != 0
+ * -> UNSUPPORTED.  Waits on the context's stream. */
+int lbm_set_shift_velocity(lbm_ctx* ctx, double ux_ref, double uy_ref);
+
 /* f(x, 0) = f^eq(rho(x), u(x)) (Sec. 5a initial state; Eq. extendedFeq), computed in FP64
  * and rounded to the storage type; resets the step counter and the blow-up status. */
 int lbm_init_equilibrium(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
@@ -185,10 +193,84 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
 int lbm_group_step(lbm_group* g, long long nsteps);
 void lbm_group_destroy(lbm_group* g);
 /* Optional live timing of the graph replays with CUDA events on the group's stream:
- * enable, then read the summed duration (ms) of the replays and the number of step-kernel
- * launches they contained (waits on the stream). */
+ * enable, then read the summed duration (ms) of the replays, the number of lattice time
+ * steps and the number of step-kernel launches they contained (waits on the stream).
+ * A group of 2-16 contexts of one storage type advances all of them with one multi-lattice
+ * launch per time step; otherwise each context gets its own launch. */
 int lbm_group_set_timing(lbm_group* g, int enable);
-int lbm_group_timing(lbm_group* g, double* replay_ms, long long* step_launches);
+int lbm_group_timing(lbm_group* g, double* replay_ms, long long* lattice_steps, long long* kernel_launches);
+
+/* Discrete adjoint of N steps (Eq. StreamCollide): lambda^n = dL/df^n runs backwards as
+ *   lambda^n_j(x) = sum_i lambda^{n+1}_i(x + xi_i) dC_i/df_j(f^n(x))
+ * (reverse streaming, then the transposed per-node collision Jacobian J of App. A,
+ * Eq. Perturbed_Collision, taken at each node's own state), with the gradients
+ *   dL/domega_k = sum_n sum_x sum_i lambda^{n+1}_i(x + xi_i) dC_i/domega_k   (FP64 sums),
+ *   dL/du0_a(x) = sum_i lambda^0_i(x) df^eq_i/du_a(rho0(x), u0(x)).
+ * The current state of the context is taken as f^0 = f^eq(rho0, u0) (call
+ * lbm_init_equilibrium first); the call advances it to f^N.  Loss: 0 = misfit
+ * L = 1/2 sum_x |u^N(x) - u*(x)|^2 with u* = (ux_target, uy_target) [ny][nx]; 1 = kinetic
+ * energy L = 1/2 sum_x rho |u|^2 (targets ignored).  Memory: ceil(N/K) checkpoints plus K
+ * recomputed states, K = checkpoint_every (0: ceil(sqrt(N))).  Outputs: grad_ux0/grad_uy0
+ * [ny][nx], grad_rates3 = [dL/domega_nu, dL/domega3, dL/domega4] (zero for rates a model
+ * does not use), *loss_out; any may be host or device pointers.  times_ms2 (host, optional):
+ * [forward ms incl. checkpoints, backward ms incl. recomputation].
+ * The storage shift of lbm_set_shift_velocity is honoured (a shift at the mean flow keeps the
+ * FP32 trajectory, and so its gradient, closer to FP64).
+ * Errors: storage other than FP64/FP32, or eq_order 2 -> UNSUPPORTED. */
+int lbm_adjoint_run(lbm_ctx* ctx, long long nsteps, int loss, const double* ux_target, const double* uy_target,
+                    int checkpoint_every, double* grad_ux0, double* grad_uy0, double* grad_rates3,
+                    double* loss_out, double* times_ms2);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched stability sweep: many independent periodic lattices of uneven size, each with its
+ * own collision model, rates and blow-up detection, advanced by one persistent kernel launch
+ * recorded in a CUDA graph (the numerical-stability study of Sec. 5b over (model, Ma, nu)).
+ *
+ * Blow-up criterion, evaluated every `check_every` steps on the pre-collision state with FP64
+ * accumulation: any node with a non-finite rho or u, or min rho <= 0, or the perturbation
+ * energy <|u - u_ref|^2> above `growth` times its value at the first check (values below
+ * 1e-20 count as 1e-20), or, when ke_ref > 0, <|u|^2> > ke_factor * ke_ref (Sec. 5b with
+ * ke_ref = u_0^2).  A blown-up instance stops; its step of detection is reported. */
+typedef struct {
+    int nx, ny;              /* lattice size (>= 3 each, nx * ny <= 2^31)                  */
+    int model;               /* lbm_model                                                 */
+    lbm_rates rates;         /* each in (0, 2); PR uses omega3 = omega4 = 1               */
+    double ux_ref, uy_ref;   /* reference (mean-flow) velocity: of the perturbation energy
+                                and of the storage shift g = f - f^eq(rho0, u_ref); |.| < 1 */
+    double ke_ref, ke_factor;/* optional kinetic-energy criterion (ke_ref <= 0: off)      */
+} lbm_instance_desc;
+
+typedef struct lbm_batch lbm_batch;
+
+/* Lay out n instances in one device slab (two buffers each, rows 32-byte aligned) for the
+ * given storage type and shift density rho0.  Errors: invalid descriptors -> INVALID_ARG,
+ * allocation failure -> NOMEM.  *out is NULL on error. */
+int lbm_batch_create(lbm_batch** out, int n, const lbm_instance_desc* desc, int storage, double rho0,
+                     void* cuda_stream);
+void lbm_batch_destroy(lbm_batch* b);
+/* Total number of nodes over all instances (the length of the concatenated fields). */
+long long lbm_batch_nodes(const lbm_batch* b);
+/* Equilibrium initial state of every instance (Eq. extendedFeq) from concatenated dense
+ * fields: instance k's [ny][nx] block follows instance k-1's.  Host or device pointers.
+ * Resets every instance's step counter and blow-up state.  Waits on the stream. */
+int lbm_batch_init_equilibrium(lbm_batch* b, const double* rho, const double* ux, const double* uy);
+/* Advance every live instance to `target_steps` total steps (asynchronous; one graph launch
+ * of the persistent kernel).  growth > 1. */
+int lbm_batch_run(lbm_batch* b, long long target_steps, int check_every, double growth);
+/* Per-instance results (host arrays of n entries, any may be NULL; waits on the stream):
+ * status 0 or LBM_ERR_BLOWUP, step of detection (-1 if none), steps taken, and diag4 =
+ * n x [last <|u-u_ref|^2>, last <|u|^2>, last min rho, first-check <|u-u_ref|^2>]. */
+int lbm_batch_status(lbm_batch* b, int* status, long long* blowup_step, long long* steps, double* diag4);
+/* Canonical pre-collision populations of one instance as FP64 [9][ny][nx]. */
+int lbm_batch_get_populations(lbm_batch* b, int index, double* f);
+/* Kernel shape: `vec` x-nodes per thread and `block` threads per CTA.  autotune times every
+ * instantiated shape for `trial_steps` steps from the current state (restoring the state
+ * after each trial), keeps the fastest and reports it. */
+int lbm_batch_set_shape(lbm_batch* b, int vec, int block);
+int lbm_batch_get_shape(const lbm_batch* b, int* vec, int* block, int* grid);
+int lbm_batch_autotune(lbm_batch* b, long long trial_steps, int check_every, int* vec, int* block,
+                       double* best_ms);
+const char* lbm_batch_last_error(const lbm_batch* b);
 
 /* Text of the last error on this context (never NULL); lbm_error_string names a code. */
 const char* lbm_last_error(const lbm_ctx* ctx);

@@ -31,4 +31,4 @@ the paper to an external reference); its agreement with the paper's linear-stabi
 statements is "parity unpinned".
 """
 
-from . import d2q9, moments, equilibrium, collision, lbm, lsa  # noqa: F401
+from . import d2q9, moments, equilibrium, collision, lbm, lsa, adjoint  # noqa: F401

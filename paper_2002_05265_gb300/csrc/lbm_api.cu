@@ -2,6 +2,7 @@
 // time stepping with CUDA-graph replay, blow-up checks and multi-lattice groups.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -21,6 +22,7 @@ struct lbm_ctx {
     int nx = 0, ny = 0, pitch = 0, nseg = 0, vec = 0;
     int model = 0, storage = 0, eq_order = 4;
     double rho0 = 1.0;
+    double urx = 0.0, ury = 0.0;       // shift reference velocity: g = f - f^eq(rho0, u_ref)
     lbm_rates rates{};
     cudaStream_t stream = nullptr;     // caller's stream; all work goes here
     long long plane = 0;               // elements per population plane
@@ -45,6 +47,11 @@ struct lbm_ctx {
 
 struct lbm_group {
     std::vector<lbm_ctx*> ctx;
+    int fused = 0;                     // one multi-lattice launch per time step
+    const void* gkernel[2] = {nullptr, nullptr};   // default shift / reference-velocity shift
+    int ggrid[2] = {0, 0};
+    std::vector<unsigned> begin;       // padded segment offsets of the contexts
+    unsigned padded_total = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;
     int graph_steps = 0;
@@ -55,8 +62,10 @@ struct lbm_group {
     std::vector<cudaEvent_t> ev;       // pairs (start, stop) of timed replays
     size_t ev_used = 0;
     double replay_ms = 0.0;
-    long long replay_launches = 0;
-    long long pending_launches = 0;
+    long long replay_lattice_steps = 0;
+    long long pending_lattice_steps = 0;
+    long long replay_kernels = 0;
+    long long pending_kernels = 0;
 };
 
 namespace {
@@ -83,14 +92,40 @@ bool rate_ok(double w) { return std::isfinite(w) && w > 0.0 && w < 2.0; }
 
 bool rates_ok(const lbm_rates& r) { return rate_ok(r.omega_nu) && rate_ok(r.omega3) && rate_ok(r.omega4); }
 
-const void* pick_kernel(int storage, int model, int eq_order) {
+const void* pick_kernel(int storage, int model, int eq_order, bool shifted) {
     switch (storage) {
-        case LBM_F64: return lbm::step_kernel_f64(model, eq_order);
-        case LBM_F32: return lbm::step_kernel_f32(model, eq_order);
-        case LBM_F16: return lbm::step_kernel_f16(model, eq_order);
-        case LBM_BF16: return lbm::step_kernel_bf16(model, eq_order);
+        case LBM_F64: return lbm::step_kernel_f64(model, eq_order, shifted);
+        case LBM_F32: return lbm::step_kernel_f32(model, eq_order, shifted);
+        case LBM_F16: return lbm::step_kernel_f16(model, eq_order, shifted);
+        case LBM_BF16: return lbm::step_kernel_bf16(model, eq_order, shifted);
         default: return nullptr;
     }
+}
+
+bool is_shifted(const lbm_ctx* c) { return c->urx != 0.0 || c->ury != 0.0; }
+
+// resident-CTA grid for a kernel, capped by the warps of work
+int resident_grid(const void* kernel, int block, long long work_threads) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    long long g = (long long)sms * per_sm;
+    const long long need = (work_threads + block - 1) / block;
+    if (need < g) g = need;
+    return (int)(g < 1 ? 1 : g);
+}
+
+int select_kernel(lbm_ctx* c) {
+    const void* k = pick_kernel(c->storage, c->model, c->eq_order, is_shifted(c));
+    if (!k) return set_err(c, LBM_ERR_UNSUPPORTED, "no kernel for this configuration");
+    c->kernel = k;
+    const long long work = ((long long)c->ny * c->nseg + 31) / 32 * 32;
+    c->grid = resident_grid(k, c->block, work);
+    return LBM_OK;
 }
 
 StepArgs step_args(const lbm_ctx* c) {
@@ -100,13 +135,26 @@ StepArgs step_args(const lbm_ctx* c) {
     a.w3 = (c->model == LBM_PR) ? 1.0 : c->rates.omega3;
     a.w4 = (c->model == LBM_PR) ? 1.0 : c->rates.omega4;
     a.rho0 = c->rho0;
+    a.urx = c->urx;
+    a.ury = c->ury;
     return a;
 }
 
 FieldArgs field_args(const lbm_ctx* c) {
     FieldArgs a;
     a.nx = c->nx; a.ny = c->ny; a.pitch = c->pitch; a.plane = c->plane; a.rho0 = c->rho0;
+    a.urx = c->urx; a.ury = c->ury;
     return a;
+}
+
+const void* pick_group_kernel(int storage, bool shifted) {
+    switch (storage) {
+        case LBM_F64: return lbm::group_kernel_f64(shifted);
+        case LBM_F32: return lbm::group_kernel_f32(shifted);
+        case LBM_F16: return lbm::group_kernel_f16(shifted);
+        case LBM_BF16: return lbm::group_kernel_bf16(shifted);
+        default: return nullptr;
+    }
 }
 
 // true when p is device-accessible memory the kernels may read/write directly
@@ -143,6 +191,46 @@ int launch_step_once(lbm_ctx* c, cudaStream_t s) {
     return LBM_OK;
 }
 
+// one time step of every context of a fused group, as one multi-lattice launch (all contexts
+// must agree on the default vs reference-velocity shift)
+int launch_group_once(lbm_group* g, cudaStream_t s, int sh) {
+    lbm::GroupArgs ga;
+    ga.n = (int)g->ctx.size();
+    ga.padded_total = g->padded_total;
+    for (size_t k = 0; k < g->ctx.size(); ++k) {
+        lbm_ctx* c = g->ctx[k];
+        lbm::GroupEntry& e = ga.e[k];
+        e.src = c->buf[c->cur];
+        e.dst = c->buf[c->cur ^ 1];
+        e.a = step_args(c);
+        e.model = c->model;
+        e.eq_order = c->eq_order;
+        e.begin = g->begin[k];
+        e.total = (unsigned)c->ny * (unsigned)c->nseg;
+    }
+    void* args[] = {(void*)&ga};
+    LBM_CK(g->ctx[0], cudaLaunchKernel(g->gkernel[sh], dim3(g->ggrid[sh]), dim3(256), args, 0, s));
+    for (lbm_ctx* c : g->ctx) {
+        c->cur ^= 1;
+        c->steps += 1;
+    }
+    return LBM_OK;
+}
+
+int group_step_once(lbm_group* g, cudaStream_t s) {
+    if (g->fused) {
+        int nsh = 0;
+        for (lbm_ctx* c : g->ctx) nsh += is_shifted(c) ? 1 : 0;
+        if (nsh == 0) return launch_group_once(g, s, 0);
+        if (nsh == (int)g->ctx.size()) return launch_group_once(g, s, 1);
+    }
+    for (lbm_ctx* c : g->ctx) {
+        int rc = launch_step_once(c, s);
+        if (rc != LBM_OK) return rc;
+    }
+    return LBM_OK;
+}
+
 int launch_check(lbm_ctx* c, double* out8_dev, int apply) {
     CheckArgs ck;
     ck.ke_ref = c->ke_ref; ck.ke_factor = c->ke_factor; ck.uref_x = c->uref_x; ck.uref_y = c->uref_y;
@@ -166,11 +254,7 @@ int group_record(lbm_group* g) {
     for (size_t k = 0; k < g->ctx.size(); ++k) { cur0[k] = g->ctx[k]->cur; steps0[k] = g->ctx[k]->steps; }
     LBM_CK(c0, cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
     int rc = LBM_OK;
-    for (int t = 0; t < g->graph_steps && rc == LBM_OK; ++t)
-        for (lbm_ctx* c : g->ctx) {
-            rc = launch_step_once(c, g->capture);
-            if (rc != LBM_OK) break;
-        }
+    for (int t = 0; t < g->graph_steps && rc == LBM_OK; ++t) rc = group_step_once(g, g->capture);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(g->capture, &graph);
     for (size_t k = 0; k < g->ctx.size(); ++k) { g->ctx[k]->cur = cur0[k]; g->ctx[k]->steps = steps0[k]; }
@@ -217,7 +301,8 @@ int group_replay(lbm_group* g) {
     LBM_CK(c0, cudaGraphLaunch(g->exec, g->stream));
     if (g->timing) {
         LBM_CK(c0, cudaEventRecord(e1, g->stream));
-        g->pending_launches += (long long)g->graph_steps * (long long)g->ctx.size();
+        g->pending_lattice_steps += (long long)g->graph_steps * (long long)g->ctx.size();
+        g->pending_kernels += (long long)g->graph_steps * (g->fused ? 1LL : (long long)g->ctx.size());
     }
     for (lbm_ctx* c : g->ctx) c->steps += g->graph_steps;   // even: buffers end where they began
     return LBM_OK;
@@ -276,11 +361,11 @@ int lbm_create(lbm_ctx** out, int nx, int ny, int periodic, int model, lbm_rates
     c->pitch = (nx + 31) / 32 * 32;
     c->nseg = (nx + c->vec - 1) / c->vec;
     c->plane = (long long)ny * c->pitch;
-    c->kernel = pick_kernel(storage, model, eq_order);
     int rc = LBM_OK;
     const size_t bytes = (size_t)9 * (size_t)c->plane * (size_t)lbm::storage_bytes(storage);
     do {
-        if (!c->kernel) { rc = set_err(c, LBM_ERR_UNSUPPORTED, "no kernel for this configuration"); break; }
+        rc = select_kernel(c);
+        if (rc != LBM_OK) break;
         cudaError_t e;
         for (int b = 0; b < 2; ++b) {
             e = cudaMalloc(&c->buf[b], bytes);
@@ -305,17 +390,6 @@ int lbm_create(lbm_ctx** out, int nx, int ny, int periodic, int model, lbm_rates
             set_err(c, rc, "create: %s", cudaGetErrorString(e));
             break;
         }
-        // grid: resident CTAs of the whole GPU (grid-stride loop inside the kernel)
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c->kernel, c->block, 0);
-        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-        const long long work_warps = ((long long)ny * c->nseg + 31) / 32;
-        long long g = (long long)sms * per_sm;
-        const long long need = (work_warps * 32 + c->block - 1) / c->block;
-        if (need < g) g = need;
-        c->grid = (int)(g < 1 ? 1 : g);
     } while (0);
     if (rc != LBM_OK) {
         lbm_destroy(c);
@@ -343,6 +417,27 @@ int lbm_set_rates(lbm_ctx* c, lbm_rates r) {
     c->rates = r;
     c->gen += 1;   // kernel arguments are baked into recorded graphs
     return LBM_OK;
+}
+
+int lbm_set_shift_velocity(lbm_ctx* c, double urx, double ury) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!std::isfinite(urx) || !std::isfinite(ury) || std::fabs(urx) >= 1.0 || std::fabs(ury) >= 1.0)
+        return set_err(c, LBM_ERR_INVALID_ARG, "shift velocity must be finite with |u| < 1");
+    if (c->eq_order == 2 && (urx != 0.0 || ury != 0.0))
+        return set_err(c, LBM_ERR_UNSUPPORTED, "a shift velocity needs the extended equilibrium");
+    if (urx == c->urx && ury == c->ury) return LBM_OK;
+    // re-encode the current state: gather f with the old shift, scatter with the new one
+    const size_t n = (size_t)c->nx * c->ny;
+    int rc = ensure_stage(c, 9 * n);
+    if (rc) return rc;
+    LBM_CK(c, lbm::launch_gather(c->storage, c->buf[c->cur], field_args(c), c->stage, nullptr, nullptr, nullptr,
+                                 nullptr, nullptr, nullptr, c->stream));
+    c->urx = urx;
+    c->ury = ury;
+    LBM_CK(c, lbm::launch_scatter(c->storage, c->buf[c->cur], field_args(c), c->stage, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    c->gen += 1;
+    return select_kernel(c);
 }
 
 int lbm_init_equilibrium(lbm_ctx* c, const double* rho, const double* ux, const double* uy) {
@@ -493,6 +588,23 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
     g->ctx.assign(ctxs, ctxs + n);
     g->stream = ctxs[0]->stream;
     g->graph_steps = graph_steps;
+    // several lattices of one storage type: one fused launch per time step
+    bool same = n > 1 && n <= lbm::kGroupMax;
+    for (int k = 1; same && k < n; ++k) same = ctxs[k]->storage == ctxs[0]->storage;
+    if (same) {
+        unsigned off = 0;
+        for (int k = 0; k < n; ++k) {
+            g->begin.push_back(off);
+            const unsigned segs = (unsigned)ctxs[k]->ny * (unsigned)ctxs[k]->nseg;
+            off += (segs + 31u) / 32u * 32u;
+        }
+        g->padded_total = off;
+        for (int sh = 0; sh < 2; ++sh) {
+            g->gkernel[sh] = pick_group_kernel(ctxs[0]->storage, sh == 1);
+            g->ggrid[sh] = resident_grid(g->gkernel[sh], 256, off);
+        }
+        g->fused = 1;
+    }
     if (graph_steps > 0) {
         cudaError_t e = cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
@@ -530,11 +642,10 @@ int lbm_group_step(lbm_group* g, long long nsteps) {
             if (rc) return rc;
             left -= g->graph_steps;
         }
-        for (long long t = 0; t < left; ++t)
-            for (lbm_ctx* c : g->ctx) {
-                int rc = launch_step_once(c, g->stream);
-                if (rc) return rc;
-            }
+        for (long long t = 0; t < left; ++t) {
+            int rc = group_step_once(g, g->stream);
+            if (rc) return rc;
+        }
         done += chunk;
         for (lbm_ctx* c : g->ctx)
             if (c->check_every > 0 && c->steps % c->check_every == 0) {
@@ -550,12 +661,14 @@ int lbm_group_set_timing(lbm_group* g, int enable) {
     g->timing = enable ? 1 : 0;
     g->ev_used = 0;
     g->replay_ms = 0.0;
-    g->replay_launches = 0;
-    g->pending_launches = 0;
+    g->replay_lattice_steps = 0;
+    g->pending_lattice_steps = 0;
+    g->replay_kernels = 0;
+    g->pending_kernels = 0;
     return LBM_OK;
 }
 
-int lbm_group_timing(lbm_group* g, double* replay_ms, long long* step_launches) {
+int lbm_group_timing(lbm_group* g, double* replay_ms, long long* lattice_steps, long long* kernel_launches) {
     if (!g) return LBM_ERR_INVALID_ARG;
     lbm_ctx* c0 = g->ctx[0];
     LBM_CK(c0, cudaStreamSynchronize(g->stream));
@@ -565,10 +678,176 @@ int lbm_group_timing(lbm_group* g, double* replay_ms, long long* step_launches) 
         g->replay_ms += ms;
     }
     g->ev_used = 0;
-    g->replay_launches += g->pending_launches;
-    g->pending_launches = 0;
+    g->replay_lattice_steps += g->pending_lattice_steps;
+    g->pending_lattice_steps = 0;
+    g->replay_kernels += g->pending_kernels;
+    g->pending_kernels = 0;
     if (replay_ms) *replay_ms = g->replay_ms;
-    if (step_launches) *step_launches = g->replay_launches;
+    if (lattice_steps) *lattice_steps = g->replay_lattice_steps;
+    if (kernel_launches) *kernel_launches = g->replay_kernels;
+    return LBM_OK;
+}
+
+int lbm_adjoint_run(lbm_ctx* c, long long nsteps, int loss, const double* ux_target, const double* uy_target,
+                    int checkpoint_every, double* grad_ux0, double* grad_uy0, double* grad_rates3, double* loss_out,
+                    double* times_ms2) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (nsteps < 1 || (loss != 0 && loss != 1) || checkpoint_every < 0 || !grad_ux0 || !grad_uy0 || !grad_rates3 ||
+        !loss_out || (loss == 0 && (!ux_target || !uy_target)))
+        return set_err(c, LBM_ERR_INVALID_ARG, "invalid adjoint arguments");
+    if ((c->storage != LBM_F64 && c->storage != LBM_F32) || c->eq_order != 4)
+        return set_err(c, LBM_ERR_UNSUPPORTED, "the adjoint supports FP64/FP32 storage and the extended equilibrium");
+    const StepArgs sa = step_args(c);
+    lbm::AdjointPlan plan;
+    int rc = lbm::adjoint_plan(c->storage, c->model, c->nx, c->ny, c->pitch, c->plane, sa.w_nu, sa.w3, sa.w4, c->rho0,
+                               c->urx, c->ury, &plan);
+    if (rc) return set_err(c, rc, "no adjoint kernel for this configuration");
+    const long long N = nsteps;
+    long long K = checkpoint_every > 0 ? checkpoint_every : (long long)std::ceil(std::sqrt((double)N));
+    if (checkpoint_every <= 0 && K % 2) ++K;   // even segments keep the lambda parity fixed
+    if (K > N) K = N;
+    const long long nseg = (N + K - 1) / K;
+    const size_t n = (size_t)c->nx * c->ny;
+    const size_t bufb = (size_t)9 * c->plane * lbm::storage_bytes(c->storage);
+    const size_t lamb = (size_t)9 * c->plane * (c->storage == LBM_F64 ? sizeof(double) : sizeof(float));
+    char* ckpt = nullptr;
+    char* ring = nullptr;
+    char* lam = nullptr;
+    double* rate_part = nullptr;
+    double* loss_part = nullptr;
+    double* dev_io = nullptr;   // targets (2n) and gradients (2n) staged on the device
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    std::vector<double> rp((size_t)plan.grid_adj * 3), lp((size_t)lbm::adjoint_seed_blocks());
+    const bool tdev = loss == 1 || (is_device_ptr(ux_target) && is_device_ptr(uy_target));
+    const bool gdev = is_device_ptr(grad_ux0) && is_device_ptr(grad_uy0);
+    cudaError_t e = cudaSuccess;
+    const double* uxt = ux_target;
+    const double* uyt = uy_target;
+    double* gux = grad_ux0;
+    double* guy = grad_uy0;
+    int cur_l = 0;
+    float fwd_ms = 0.f, bwd_ms = 0.f;
+#define LBM_ADJ(call) do { if (e == cudaSuccess) e = (call); } while (0)
+    LBM_ADJ(cudaMalloc(&ckpt, (size_t)nseg * bufb));
+    LBM_ADJ(cudaMalloc(&ring, (size_t)K * bufb));
+    LBM_ADJ(cudaMalloc(&lam, 2 * lamb));
+    LBM_ADJ(cudaMalloc(&rate_part, rp.size() * sizeof(double)));
+    LBM_ADJ(cudaMalloc(&loss_part, lp.size() * sizeof(double)));
+    LBM_ADJ(cudaMalloc(&dev_io, 4 * n * sizeof(double)));
+    for (int k = 0; k < 3; ++k) LBM_ADJ(cudaEventCreate(&ev[k]));
+    if (e == cudaSuccess && !tdev) {
+        LBM_ADJ(cudaMemcpyAsync(dev_io, ux_target, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        LBM_ADJ(cudaMemcpyAsync(dev_io + n, uy_target, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        uxt = dev_io;
+        uyt = dev_io + n;
+    }
+    if (!gdev) {
+        gux = dev_io + 2 * n;
+        guy = dev_io + 3 * n;
+    }
+    // forward: checkpoint every K steps
+    LBM_ADJ(cudaEventRecord(ev[0], c->stream));
+    for (long long s2 = 0; s2 < nseg && e == cudaSuccess; ++s2) {
+        LBM_ADJ(cudaMemcpyAsync(ckpt + s2 * bufb, c->buf[c->cur], bufb, cudaMemcpyDeviceToDevice, c->stream));
+        if (e == cudaSuccess) {
+            const int r = lbm_step(c, std::min(K, N - s2 * K));
+            if (r != LBM_OK) rc = r;
+        }
+        if (rc != LBM_OK) break;
+    }
+    LBM_ADJ(cudaEventRecord(ev[1], c->stream));
+    // seed lambda^N and the loss from f^N
+    LBM_ADJ(lbm::adjoint_launch_seed(plan, c->buf[c->cur], loss, uxt, uyt, lam, loss_part, c->stream));
+    LBM_ADJ(cudaMemsetAsync(rate_part, 0, rp.size() * sizeof(double), c->stream));
+    // backward, segment by segment from the last one: restore the checkpoint, recompute the
+    // segment's states into the ring, run its adjoint steps backwards.  A full segment is one
+    // CUDA-graph replay (one graph per starting parity of the lambda ping-pong).
+    cudaGraphExec_t seg_exec[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;
+    LBM_ADJ(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    auto enqueue_segment = [&](long long len, int parity, cudaStream_t st) {
+        cudaError_t r = cudaSuccess;
+        for (long long k = 0; k + 1 < len && r == cudaSuccess; ++k)
+            r = lbm::adjoint_launch_fwd(plan, sa, ring + k * bufb, ring + (k + 1) * bufb, st);
+        int pl = parity;
+        for (long long k = len - 1; k >= 0 && r == cudaSuccess; --k) {
+            r = lbm::adjoint_launch_step(plan, ring + k * bufb, lam + pl * lamb, lam + (pl ^ 1) * lamb, rate_part, st);
+            pl ^= 1;
+        }
+        return r;
+    };
+    for (long long s2 = nseg - 1; s2 >= 0 && e == cudaSuccess && rc == LBM_OK; --s2) {
+        const long long len = std::min(K, N - s2 * K);
+        LBM_ADJ(cudaMemcpyAsync(ring, ckpt + s2 * bufb, bufb, cudaMemcpyDeviceToDevice, c->stream));
+        if (len == K && K > 1) {
+            if (!seg_exec[cur_l] && e == cudaSuccess) {
+                cudaGraph_t graph = nullptr;
+                LBM_ADJ(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+                const cudaError_t r = enqueue_segment(len, cur_l, cap);
+                const cudaError_t r2 = cudaStreamEndCapture(cap, &graph);
+                LBM_ADJ(r);
+                LBM_ADJ(r2);
+                if (graph) {
+                    LBM_ADJ(cudaGraphInstantiate(&seg_exec[cur_l], graph, 0));
+                    cudaGraphDestroy(graph);
+                }
+            }
+            LBM_ADJ(cudaGraphLaunch(seg_exec[cur_l], c->stream));
+        } else {
+            LBM_ADJ(enqueue_segment(len, cur_l, c->stream));
+        }
+        if (len % 2) cur_l ^= 1;
+    }
+    for (int k = 0; k < 2; ++k)
+        if (seg_exec[k]) cudaGraphExecDestroy(seg_exec[k]);
+    if (cap) cudaStreamDestroy(cap);
+    // dL/du0 from lambda^0 and the initial state (checkpoint 0)
+    LBM_ADJ(lbm::adjoint_launch_init(plan, ckpt, lam + cur_l * lamb, gux, guy, c->stream));
+    LBM_ADJ(cudaEventRecord(ev[2], c->stream));
+    if (!gdev) {
+        LBM_ADJ(cudaMemcpyAsync(grad_ux0, gux, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        LBM_ADJ(cudaMemcpyAsync(grad_uy0, guy, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    LBM_ADJ(cudaMemcpyAsync(rp.data(), rate_part, rp.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LBM_ADJ(cudaMemcpyAsync(lp.data(), loss_part, lp.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LBM_ADJ(cudaStreamSynchronize(c->stream));
+    if (e == cudaSuccess) {
+        cudaEventElapsedTime(&fwd_ms, ev[0], ev[1]);
+        cudaEventElapsedTime(&bwd_ms, ev[1], ev[2]);
+    }
+#undef LBM_ADJ
+    cudaFree(ckpt);
+    cudaFree(ring);
+    cudaFree(lam);
+    cudaFree(rate_part);
+    cudaFree(loss_part);
+    cudaFree(dev_io);
+    for (int k = 0; k < 3; ++k)
+        if (ev[k]) cudaEventDestroy(ev[k]);
+    if (rc != LBM_OK) return rc;
+    if (e != cudaSuccess)
+        return set_err(c, e == cudaErrorMemoryAllocation ? LBM_ERR_NOMEM : LBM_ERR_CUDA, "adjoint: %s",
+                       cudaGetErrorString(e));
+    // fixed-order FP64 folds of the per-block partials
+    double gr[3] = {0.0, 0.0, 0.0}, L = 0.0;
+    for (size_t b = 0; b < rp.size() / 3; ++b)
+        for (int k = 0; k < 3; ++k) gr[k] += rp[b * 3 + k];
+    for (double v : lp) L += v;
+    if (c->model == LBM_PR) gr[1] = gr[2] = 0.0;
+    if (is_device_ptr(grad_rates3)) {
+        LBM_CK(c, cudaMemcpy(grad_rates3, gr, sizeof(gr), cudaMemcpyHostToDevice));
+    } else {
+        for (int k = 0; k < 3; ++k) grad_rates3[k] = gr[k];
+    }
+    if (is_device_ptr(loss_out)) {
+        LBM_CK(c, cudaMemcpy(loss_out, &L, sizeof(L), cudaMemcpyHostToDevice));
+    } else {
+        *loss_out = L;
+    }
+    if (times_ms2) {
+        times_ms2[0] = fwd_ms;
+        times_ms2[1] = bwd_ms;
+    }
     return LBM_OK;
 }
 

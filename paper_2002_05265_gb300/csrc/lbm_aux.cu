@@ -39,17 +39,19 @@ __global__ void init_eq_kernel(S* buf, FieldArgs a, int eq_order, const double* 
             const int sx = ex_of(i), sy = ey_of(i);
             double g;
             if (eq_order == 4) {
-                // Eq. extendedFeq in product form, minus w_i rho0
-                const double Wx = sx ? 1.0 / 6.0 : 2.0 / 3.0, Wy = sy ? 1.0 / 6.0 : 2.0 / 3.0;
-                const double dx = sx ? 0.5 * (vx * vx + sx * vx) : -vx * vx;
-                const double dy = sy ? 0.5 * (vy * vy + sy * vy) : -vy * vy;
-                g = Wx * Wy * dr + r * (Wx * dy + dx * (Wy + dy));
+                // Eq. extendedFeq in product form minus the shift s_i = rho0 P_sx P_sy, with
+                // P_s = phi_s(u_ref) and D_s = phi_s(u) - phi_s(u_ref) written as differences
+                const double Px = phi1d(sx, a.urx), Py = phi1d(sy, a.ury);
+                const double dux = vx - a.urx, sux = vx + a.urx, duy = vy - a.ury, suy = vy + a.ury;
+                const double Dx = sx ? 0.5 * dux * (sux + sx) : -dux * sux;
+                const double Dy = sy ? 0.5 * duy * (suy + sy) : -duy * suy;
+                g = Px * Py * dr + r * (Px * Dy + Dx * (Py + Dy));
             } else {
                 const double wi = weight_of(i);
                 const double eu = 3.0 * (sx * vx + sy * vy);
                 g = wi * dr + wi * r * (eu + 0.5 * eu * eu - 1.5 * (vx * vx + vy * vy));
             }
-            buf[src_offset(i, x, y, a)] = Store<S>::from_double(g);
+            buf[src_offset(i, x, y, a)] = Conv<S>::from_double(g);
         }
     }
 }
@@ -61,7 +63,7 @@ __global__ void scatter_kernel(S* buf, FieldArgs a, const double* __restrict__ f
         const int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            buf[src_offset(i, x, y, a)] = Store<S>::from_double(f[i * n + k] - weight_of(i) * a.rho0);
+            buf[src_offset(i, x, y, a)] = Conv<S>::from_double(f[i * n + k] - shift_of(i, a.rho0, a.urx, a.ury));
     }
 }
 
@@ -73,10 +75,10 @@ __global__ void gather_kernel(const S* buf, FieldArgs a, double* f, double* rho,
         const int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
         double g[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = Store<S>::to_double(buf[src_offset(i, x, y, a)]);
+        for (int i = 0; i < 9; ++i) g[i] = Conv<S>::to_double(buf[src_offset(i, x, y, a)]);
         if (f) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) f[i * n + k] = g[i] + weight_of(i) * a.rho0;
+            for (int i = 0; i < 9; ++i) f[i * n + k] = g[i] + shift_of(i, a.rho0, a.urx, a.ury);
         }
         if (rho || ux || uy || pxx || pxy || pyy) {
             double dr = 0, jx = 0, jy = 0, sxx = 0, sxy = 0, syy = 0;
@@ -86,53 +88,23 @@ __global__ void gather_kernel(const S* buf, FieldArgs a, double* f, double* rho,
                 dr += g[i]; jx += sx * g[i]; jy += sy * g[i];
                 sxx += sx * sx * g[i]; sxy += sx * sy * g[i]; syy += sy * sy * g[i];
             }
+            // moments of the shift: sum s = rho0, sum xi s = rho0 u_ref,
+            // sum xi_a xi_b s = rho0 (u_ref,a u_ref,b + c_s^2 delta_ab)
             const double r = a.rho0 + dr;
+            jx += a.rho0 * a.urx;
+            jy += a.rho0 * a.ury;
             if (rho) rho[k] = r;
             if (ux) ux[k] = jx / r;
             if (uy) uy[k] = jy / r;
-            // sum_i xi_a xi_b w_i = c_s^2 delta_ab
-            if (pxx) pxx[k] = sxx + a.rho0 / 3.0;
-            if (pxy) pxy[k] = sxy;
-            if (pyy) pyy[k] = syy + a.rho0 / 3.0;
+            if (pxx) pxx[k] = sxx + a.rho0 * (a.urx * a.urx + 1.0 / 3.0);
+            if (pxy) pxy[k] = sxy + a.rho0 * a.urx * a.ury;
+            if (pyy) pyy[k] = syy + a.rho0 * (a.ury * a.ury + 1.0 / 3.0);
         }
     }
 }
 
-// Pass 1: per-node rho, u in the collision precision T, accumulated per thread in FP64,
-// then folded per block in a fixed order.  Slots: 0 sum drho, 1 sum rho ux, 2 sum rho uy,
-// 3 sum rho|u|^2/2, 4 sum |u|^2, 5 sum |u-uref|^2, 6 min rho (as drho), 7 non-finite count.
-template <typename S>
-__global__ void __launch_bounds__(kBlock) reduce_kernel(const S* buf, FieldArgs a, double* partials,
-                                                        double urefx, double urefy) {
-    using T = typename Store<S>::T;
-    const long long n = (long long)a.nx * a.ny;
-    double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
-        T dr = 0, jx = 0, jy = 0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const T g = (T)Store<S>::to_double(buf[src_offset(i, x, y, a)]);
-            dr += g;
-            jx += T(ex_of(i)) * g;
-            jy += T(ey_of(i)) * g;
-        }
-        const T r = T(a.rho0) + dr;
-        const T vx = jx / r, vy = jy / r;
-        if (isfinite(r) && isfinite(vx) && isfinite(vy)) {
-            const T u2 = vx * vx + vy * vy;
-            const T wx = vx - T(urefx), wy = vy - T(urefy);
-            acc[0] += (double)dr;
-            acc[1] += (double)jx;
-            acc[2] += (double)jy;
-            acc[3] += 0.5 * (double)(r * u2);
-            acc[4] += (double)u2;
-            acc[5] += (double)(wx * wx + wy * wy);
-            acc[6] = fmin(acc[6], (double)dr);
-        } else {
-            acc[7] += 1.0;
-        }
-    }
+// Folds the per-thread accumulators of a block in a fixed order into its partial slot.
+__device__ __forceinline__ void block_fold_partials(double (&acc)[kReduceValues], double* partials) {
     __shared__ double sh[kBlock / 32][kReduceValues];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -151,6 +123,104 @@ __global__ void __launch_bounds__(kBlock) reduce_kernel(const S* buf, FieldArgs 
         for (int w = 1; w < kBlock / 32; ++w) x = (v == 6) ? fmin(x, sh[w][v]) : x + sh[w][v];
         partials[blockIdx.x * kReduceValues + v] = x;
     }
+}
+
+// Pass 1, per-node form: the same sums for layouts whose rows are not 16-byte aligned
+// (caller-owned buffers of lbm_reduce_noalloc may have any pitch); one node per thread,
+// scalar loads.
+template <typename S>
+__global__ void __launch_bounds__(kBlock) reduce_kernel_scalar(const S* buf, FieldArgs a, double* partials,
+                                                               double urefx, double urefy) {
+    using T = typename Conv<S>::T;
+    const long long n = (long long)a.nx * a.ny;
+    const T jx0 = T(a.rho0 * a.urx), jy0 = T(a.rho0 * a.ury);
+    double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
+        T dr = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const T g = Conv<S>::to_T(buf[src_offset(i, x, y, a)]);
+            dr += g;
+            jx += T(ex_of(i)) * g;
+            jy += T(ey_of(i)) * g;
+        }
+        jx += jx0;
+        jy += jy0;
+        const T r = T(a.rho0) + dr;
+        const T vx = jx / r, vy = jy / r;
+        if (isfinite(r) && isfinite(vx) && isfinite(vy)) {
+            const T u2 = vx * vx + vy * vy;
+            const T wx = vx - T(urefx), wy = vy - T(urefy);
+            acc[0] += (double)dr;
+            acc[1] += (double)jx;
+            acc[2] += (double)jy;
+            acc[3] += 0.5 * (double)(r * u2);
+            acc[4] += (double)u2;
+            acc[5] += (double)(wx * wx + wy * wy);
+            acc[6] = fmin(acc[6], (double)dr);
+        } else {
+            acc[7] += 1.0;
+        }
+    }
+    block_fold_partials(acc, partials);
+}
+
+// Pass 1: per-node rho, u in the collision precision T from the same vectorised pull gather
+// as the step kernel, accumulated per thread in FP64, then folded per block in a fixed
+// order.  Slots: 0 sum drho, 1 sum rho ux, 2 sum rho uy, 3 sum rho|u|^2/2, 4 sum |u|^2,
+// 5 sum |u-uref|^2, 6 min rho (as drho), 7 non-finite count.
+template <typename S>
+__global__ void __launch_bounds__(kBlock) reduce_kernel(const S* buf, FieldArgs a, double* partials,
+                                                        double urefx, double urefy) {
+    using T = typename Conv<S>::T;
+    constexpr int VEC = DefaultVec<S>::value;
+    const int lane = threadIdx.x & 31;
+    const int nseg = (a.nx + VEC - 1) / VEC;
+    const unsigned total = (unsigned)a.ny * (unsigned)nseg;
+    const unsigned stride = gridDim.x * blockDim.x;
+    const T jx0 = T(a.rho0 * a.urx), jy0 = T(a.rho0 * a.ury);
+    double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
+    for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+        const unsigned s = base + lane;
+        const bool active = s < total;
+        const unsigned sc = active ? s : total - 1;
+        const int y = (int)(sc / (unsigned)nseg);
+        const int seg = (int)(sc - (unsigned)y * (unsigned)nseg);
+        const int x0 = seg * VEC;
+        const int nvalid = min(VEC, a.nx - x0);
+        T f[9][VEC];
+        gather_pull<S, VEC, 1>(buf, a.nx, a.ny, a.pitch, a.plane, y, seg, nseg, x0, nvalid, lane, f);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            if (!active || j >= nvalid) continue;
+            T dr = 0, jx = 0, jy = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                dr += f[i][j];
+                jx += T(ex_of(i)) * f[i][j];
+                jy += T(ey_of(i)) * f[i][j];
+            }
+            jx += jx0;
+            jy += jy0;
+            const T r = T(a.rho0) + dr;
+            const T vx = jx / r, vy = jy / r;
+            if (isfinite(r) && isfinite(vx) && isfinite(vy)) {
+                const T u2 = vx * vx + vy * vy;
+                const T wx = vx - T(urefx), wy = vy - T(urefy);
+                acc[0] += (double)dr;
+                acc[1] += (double)jx;
+                acc[2] += (double)jy;
+                acc[3] += 0.5 * (double)(r * u2);
+                acc[4] += (double)u2;
+                acc[5] += (double)(wx * wx + wy * wy);
+                acc[6] = fmin(acc[6], (double)dr);
+            } else {
+                acc[7] += 1.0;
+            }
+        }
+    }
+    block_fold_partials(acc, partials);
 }
 
 // Pass 2: one block folds the partials (fixed order), forms the outputs and applies the
@@ -229,7 +299,12 @@ cudaError_t gather_t(const void* buf, const FieldArgs& a, double* f, double* r, 
 template <typename S>
 cudaError_t reduce_t(const void* buf, const FieldArgs& a, double* partials, double* out8, int* status,
                      long long* blowup_step, const CheckArgs& c, cudaStream_t s) {
-    reduce_kernel<S><<<kReduceBlocks, kBlock, 0, s>>>((const S*)buf, a, partials, c.uref_x, c.uref_y);
+    // the vectorised gather needs every row start 16-byte aligned
+    const bool aligned = ((size_t)a.pitch * sizeof(S)) % 16 == 0 && ((uintptr_t)buf % 16) == 0;
+    if (aligned)
+        reduce_kernel<S><<<kReduceBlocks, kBlock, 0, s>>>((const S*)buf, a, partials, c.uref_x, c.uref_y);
+    else
+        reduce_kernel_scalar<S><<<kReduceBlocks, kBlock, 0, s>>>((const S*)buf, a, partials, c.uref_x, c.uref_y);
     reduce_finish_kernel<<<1, kBlock, 0, s>>>(partials, kReduceBlocks, a, out8, status, blowup_step, c);
     return cudaGetLastError();
 }
@@ -265,10 +340,10 @@ cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, doub
 
 int storage_vec(int storage) {
     switch (storage) {
-        case 0: return Store<double>::VEC;
-        case 1: return Store<float>::VEC;
-        case 2: return Store<__half>::VEC;
-        case 3: return Store<__nv_bfloat16>::VEC;
+        case 0: return DefaultVec<double>::value;
+        case 1: return DefaultVec<float>::value;
+        case 2: return DefaultVec<__half>::value;
+        case 3: return DefaultVec<__nv_bfloat16>::value;
         default: return 0;
     }
 }
@@ -344,6 +419,7 @@ extern "C" int lbm_reduce_noalloc(const void* populations, int storage, int nx, 
     }
     FieldArgs a;
     a.nx = nx; a.ny = ny; a.pitch = pitch; a.plane = (long long)ny * pitch; a.rho0 = rho0;
+    a.urx = 0.0; a.ury = 0.0;
     CheckArgs c;
     c.ke_ref = 0.0; c.ke_factor = 1.0; c.uref_x = uref_x; c.uref_y = uref_y; c.step = 0; c.apply = 0;
     // pass 1 overwrites every partial slot before pass 2 reads it (same stream), so nothing in

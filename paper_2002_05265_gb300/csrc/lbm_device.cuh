@@ -1,10 +1,12 @@
-// Device code of the D2Q9 stream-and-collide kernels: storage traits, the per-node collision
-// of every model of App. B written in non-equilibrium form, and the fused pull kernel.
+// Device code of the D2Q9 stream-and-collide kernels: storage conversions, the per-node
+// collision of every model of App. B written in non-equilibrium form, the per-segment pull
+// step shared by all stepping kernels, and the single-lattice and multi-lattice step kernels.
 //
-// Layout in HBM (one lattice): nine SoA planes g_i[y][x], row pitch `pitch` elements
-// (multiple of 32, so every row starts 128-byte aligned), plane = ny * pitch elements.
-// Stored values are shifted populations g_i = f_i - w_i rho0 in the storage type.
-// Two such buffers alternate: a step reads buffer A and writes buffer B.
+// Layout in HBM (one lattice): nine SoA planes g_i[y][x], row pitch `pitch` elements (rows
+// 32-byte aligned or better), plane = ny * pitch elements.  Stored values are shifted
+// populations g_i = f_i - s_i in the storage type, where the shift s_i = f^eq_i(rho0, u_ref)
+// is the extended equilibrium at a reference state; with u_ref = 0 (the default) it is
+// s_i = w_i rho0.  Two such buffers alternate: a step reads buffer A and writes buffer B.
 //
 // Buffer semantics: A_i(z) holds the post-collision population f*_i(z, t-1) emitted by node z,
 // so node x gathers its pre-collision populations as f_i(x, t) = A_i(x - xi_i) (pull form of
@@ -31,6 +33,15 @@ __host__ __device__ constexpr int ey_of(int i) {
 __host__ __device__ constexpr double weight_of(int i) {
     return (i == 0) ? 4.0 / 9.0 : ((i <= 4) ? 1.0 / 9.0 : 1.0 / 36.0);
 }
+// One-dimensional factor of the extended equilibrium (Eq. extendedFeq, product form):
+// phi_0(u) = 2/3 - u^2, phi_+-1(u) = (u^2 +- u + 1/3) / 2.
+__host__ __device__ inline double phi1d(int s, double u) {
+    return s == 0 ? 2.0 / 3.0 - u * u : 0.5 * (u * u + s * u + 1.0 / 3.0);
+}
+// Shift s_i = rho0 phi_ex(urx) phi_ey(ury) (= w_i rho0 when u_ref = 0).
+__host__ __device__ inline double shift_of(int i, double rho0, double urx, double ury) {
+    return rho0 * phi1d(ex_of(i), urx) * phi1d(ey_of(i), ury);
+}
 
 struct StepArgs {
     int nx, ny;          // lattice size
@@ -39,140 +50,185 @@ struct StepArgs {
     long long plane;     // elements per population plane
     double w_nu, w3, w4; // relaxation frequencies of orders 2, 3, 4
     double rho0;         // shift reference density
+    double urx, ury;     // shift reference velocity
 };
 
 // ---------------------------------------------------------------------------------------
-// Storage traits: VEC consecutive x-nodes move as one 16-byte vector.
-template <typename S> struct Store;
-
-template <> struct Store<double> {
+// Element conversions between the storage type S and the collision type T.
+template <typename S> struct Conv;
+template <> struct Conv<double> {
     using T = double;
-    static constexpr int VEC = 2;
-    __device__ static __forceinline__ void load(const double* p, T (&v)[VEC]) {
-        const double2 t = *reinterpret_cast<const double2*>(p);
-        v[0] = t.x; v[1] = t.y;
-    }
-    __device__ static __forceinline__ void store(double* p, const T (&v)[VEC]) {
-        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-    }
-    __device__ static __forceinline__ T load1(const double* p) { return *p; }
+    __device__ static __forceinline__ T to_T(double s) { return s; }
+    __device__ static __forceinline__ double from_T(T v) { return v; }
     __device__ static __forceinline__ double to_double(double s) { return s; }
     __device__ static __forceinline__ double from_double(double d) { return d; }
 };
-
-template <> struct Store<float> {
+template <> struct Conv<float> {
     using T = float;
-    static constexpr int VEC = 4;
-    __device__ static __forceinline__ void load(const float* p, T (&v)[VEC]) {
-        const float4 t = *reinterpret_cast<const float4*>(p);
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    }
-    __device__ static __forceinline__ void store(float* p, const T (&v)[VEC]) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-    __device__ static __forceinline__ T load1(const float* p) { return *p; }
+    __device__ static __forceinline__ T to_T(float s) { return s; }
+    __device__ static __forceinline__ float from_T(T v) { return v; }
     __device__ static __forceinline__ double to_double(float s) { return (double)s; }
     __device__ static __forceinline__ float from_double(double d) { return __double2float_rn(d); }
 };
-
-template <> struct Store<__half> {
+template <> struct Conv<__half> {
     using T = float;
-    static constexpr int VEC = 8;
-    __device__ static __forceinline__ void load(const __half* p, T (&v)[VEC]) {
-        const uint4 t = *reinterpret_cast<const uint4*>(p);
-        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            __half2 h = *reinterpret_cast<const __half2*>(&w[k]);
-            const float2 f = __half22float2(h);
-            v[2 * k] = f.x; v[2 * k + 1] = f.y;
-        }
-    }
-    __device__ static __forceinline__ void store(__half* p, const T (&v)[VEC]) {
-        uint32_t w[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            __half2 h = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
-            w[k] = *reinterpret_cast<uint32_t*>(&h);
-        }
-        *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    __device__ static __forceinline__ T load1(const __half* p) { return __half2float(*p); }
+    __device__ static __forceinline__ T to_T(__half s) { return __half2float(s); }
+    __device__ static __forceinline__ __half from_T(T v) { return __float2half_rn(v); }
     __device__ static __forceinline__ double to_double(__half s) { return (double)__half2float(s); }
     __device__ static __forceinline__ __half from_double(double d) { return __double2half(d); }
 };
-
-template <> struct Store<__nv_bfloat16> {
+template <> struct Conv<__nv_bfloat16> {
     using T = float;
-    static constexpr int VEC = 8;
-    __device__ static __forceinline__ void load(const __nv_bfloat16* p, T (&v)[VEC]) {
-        const uint4 t = *reinterpret_cast<const uint4*>(p);
-        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[k]);
-            const float2 f = __bfloat1622float2(h);
-            v[2 * k] = f.x; v[2 * k + 1] = f.y;
-        }
-    }
-    __device__ static __forceinline__ void store(__nv_bfloat16* p, const T (&v)[VEC]) {
-        uint32_t w[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-            w[k] = *reinterpret_cast<uint32_t*>(&h);
-        }
-        *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    __device__ static __forceinline__ T load1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    __device__ static __forceinline__ T to_T(__nv_bfloat16 s) { return __bfloat162float(s); }
+    __device__ static __forceinline__ __nv_bfloat16 from_T(T v) { return __float2bfloat16_rn(v); }
     __device__ static __forceinline__ double to_double(__nv_bfloat16 s) { return (double)__bfloat162float(s); }
     __device__ static __forceinline__ __nv_bfloat16 from_double(double d) { return __double2bfloat16(d); }
 };
 
+// Default vector width: VEC consecutive x-nodes of one row move as one access of
+// VEC * sizeof(S) bytes: 16 bytes for FP64 and FP32; for the 16-bit types LBM_HALF_VEC
+// nodes (8 = 16-byte accesses, 4 = 8-byte accesses and about half the registers).
+#ifndef LBM_HALF_VEC
+#define LBM_HALF_VEC 8
+#endif
+template <typename S> struct DefaultVec {
+    static constexpr int value = (sizeof(S) == 2) ? LBM_HALF_VEC : 16 / (int)sizeof(S);
+};
+
+template <int BYTES> struct Raw;
+template <> struct Raw<4> { using type = uint32_t; };
+template <> struct Raw<8> { using type = uint2; };
+template <> struct Raw<16> { using type = uint4; };
+
+// aligned vector load / store of VEC elements (VEC * sizeof(S) in {4, 8, 16} bytes)
+template <typename S, int VEC>
+__device__ __forceinline__ void vload(const S* p, typename Conv<S>::T (&v)[VEC]) {
+    using R = typename Raw<VEC * (int)sizeof(S)>::type;
+    const R r = *reinterpret_cast<const R*>(p);
+    S e[VEC];
+    memcpy(e, &r, sizeof(R));
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) v[j] = Conv<S>::to_T(e[j]);
+}
+// pairs of floats rounded to a packed pair of 16-bit values in one conversion
+__device__ __forceinline__ uint32_t pack2(__half, float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16, float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+template <typename S, int VEC>
+__device__ __forceinline__ void vstore(S* p, const typename Conv<S>::T (&v)[VEC]) {
+    using R = typename Raw<VEC * (int)sizeof(S)>::type;
+    R r;
+    if constexpr (sizeof(S) == 2) {
+        uint32_t w[VEC / 2];
+#pragma unroll
+        for (int k = 0; k < VEC / 2; ++k) w[k] = pack2(S(), v[2 * k], v[2 * k + 1]);
+        memcpy(&r, w, sizeof(R));
+    } else {
+        S e[VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) e[j] = Conv<S>::from_T(v[j]);
+        memcpy(&r, e, sizeof(R));
+    }
+    *reinterpret_cast<R*>(p) = r;
+}
+
+// Correctly rounded reciprocal (the reciprocal intrinsic instead of a full division).
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+
+// Per-launch constants of the collision in the collision precision.
+template <typename T> struct Consts {
+    T w, w3, w4, rho0, urx, ury;
+    T Px[3], Py[3];      // phi_s(u_ref) for s = 0, +1, -1 (shift factors)
+};
+template <typename T>
+__device__ __forceinline__ Consts<T> make_consts(const StepArgs& a) {
+    Consts<T> c;
+    c.w = (T)a.w_nu; c.w3 = (T)a.w3; c.w4 = (T)a.w4; c.rho0 = (T)a.rho0;
+    c.urx = (T)a.urx; c.ury = (T)a.ury;
+    c.Px[0] = (T)phi1d(0, a.urx); c.Px[1] = (T)phi1d(1, a.urx); c.Px[2] = (T)phi1d(-1, a.urx);
+    c.Py[0] = (T)phi1d(0, a.ury); c.Py[1] = (T)phi1d(1, a.ury); c.Py[2] = (T)phi1d(-1, a.ury);
+    return c;
+}
+
 // ---------------------------------------------------------------------------------------
-// Per-node collision (App. B) on shifted populations g_i = f_i - w_i rho0.
+// Per-node collision (App. B) on shifted populations g_i = f_i - s_i.
 //
 // Every model of App. B relaxes the moments of f towards those of f^eq with the same rho
 // and u, through a transform that is linear in f for the node's u.  So each model can be
 // written as f* = f^eq + T(u)^-1 [ (1 - omega_n) T(u) f^neq ] with f^neq = f - f^eq, where
 // the conserved (order 0 and 1) non-equilibrium moments are exactly zero.  Working with
-// f^neq and the deviation g^eq = f^eq - w rho0 keeps every intermediate small, which is what
+// f^neq and the deviation g^eq = f^eq - s keeps every intermediate small, which is what
 // makes FP32 arithmetic on FP16-stored populations accurate.  The cumulant model adds the
 // C22 product terms, the recursive regularized model the recursion of Eq. RRformulas_D2Q9.
-template <int MODEL, int EQ, typename T>
-__device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], T w, T w3, T w4, T rho0) {
+// rho, ux, uy of the pre-collision state are returned for diagnostics.  SHIFT = false is the
+// default shift s = w rho0 (u_ref = 0) with compile-time weights, which keeps the shift
+// constants out of registers.
+template <int MODEL, int EQ, typename T, bool SHIFT>
+__device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], const Consts<T>& c, T& rho_out, T& ux_out,
+                                        T& uy_out) {
     const T cs2 = T(1) / T(3);
-    // density and velocity (Sec. 1): sums of the shifted populations
+    const T w = c.w, w3 = c.w3, w4 = c.w4;
+    // density and velocity (Sec. 1): sum s_i = rho0, sum xi_i s_i = rho0 u_ref
     const T drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    const T rho = rho0 + drho;
-    const T jx = (g[1] - g[3]) + ((g[5] - g[7]) + (g[8] - g[6]));
-    const T jy = (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
-    const T irho = T(1) / rho;
+    const T rho = c.rho0 + drho;
+    T jx = (g[1] - g[3]) + ((g[5] - g[7]) + (g[8] - g[6]));
+    T jy = (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
+    if (SHIFT) {
+        jx += c.rho0 * c.urx;
+        jy += c.rho0 * c.ury;
+    }
+    const T irho = recip(rho);
     const T ux = jx * irho, uy = jy * irho;
     const T uxx = ux * ux, uyy = uy * uy;
+    rho_out = rho; ux_out = ux; uy_out = uy;
 
-    // g^eq_i = f^eq_i - w_i rho0
+    // g^eq_i = f^eq_i - s_i
     T geq[9];
     if (EQ == 4) {
-        // Eq. extendedFeq, product form: f^eq_(sx,sy) = rho phi_sx(u_x) phi_sy(u_y) with
-        // phi_s = W_s + d_s: W_0 = 2/3, W_+-1 = 1/6, d_0 = -u^2, d_+-1 = (u^2 +- u)/2.
-        const T W0 = T(2) / T(3), W1 = T(1) / T(6);
-        const T dx0 = -uxx, dxp = T(0.5) * (uxx + ux), dxm = T(0.5) * (uxx - ux);
-        const T dy0 = -uyy, dyp = T(0.5) * (uyy + uy), dym = T(0.5) * (uyy - uy);
-        // rho * (W_a d_b + d_a W_b + d_a d_b) + W_a W_b drho
-#define LBM_GEQ(Wa, da, Wb, db) ((Wa) * (Wb) * drho + rho * ((Wa) * (db) + (da) * ((Wb) + (db))))
-        geq[0] = LBM_GEQ(W0, dx0, W0, dy0);
-        geq[1] = LBM_GEQ(W1, dxp, W0, dy0);
-        geq[2] = LBM_GEQ(W0, dx0, W1, dyp);
-        geq[3] = LBM_GEQ(W1, dxm, W0, dy0);
-        geq[4] = LBM_GEQ(W0, dx0, W1, dym);
-        geq[5] = LBM_GEQ(W1, dxp, W1, dyp);
-        geq[6] = LBM_GEQ(W1, dxm, W1, dyp);
-        geq[7] = LBM_GEQ(W1, dxm, W1, dym);
-        geq[8] = LBM_GEQ(W1, dxp, W1, dym);
+        // Eq. extendedFeq, product form: f^eq_(sx,sy) = rho phi_sx(u_x) phi_sy(u_y), written as
+        // phi_s(u) = P_s + D_s with P_s = phi_s(u_ref) and the difference
+        // D_0 = -(u - ur)(u + ur), D_+-1 = (u - ur)((u + ur) +- 1) / 2:
+        // f^eq - s = drho P_a P_b + rho (P_a D_b + D_a (P_b + D_b))
+        T Dx0, Dxp, Dxm, Dy0, Dyp, Dym, Px0, Pxp, Pxm, Py0, Pyp, Pym;
+        if (SHIFT) {
+            const T dux = ux - c.urx, sux = ux + c.urx, duy = uy - c.ury, suy = uy + c.ury;
+            Dx0 = -dux * sux; Dxp = T(0.5) * (dux * (sux + T(1))); Dxm = T(0.5) * (dux * (sux - T(1)));
+            Dy0 = -duy * suy; Dyp = T(0.5) * (duy * (suy + T(1))); Dym = T(0.5) * (duy * (suy - T(1)));
+            Px0 = c.Px[0]; Pxp = c.Px[1]; Pxm = c.Px[2];
+            Py0 = c.Py[0]; Pyp = c.Py[1]; Pym = c.Py[2];
+        } else {
+            Dx0 = -uxx; Dxp = T(0.5) * (uxx + ux); Dxm = T(0.5) * (uxx - ux);
+            Dy0 = -uyy; Dyp = T(0.5) * (uyy + uy); Dym = T(0.5) * (uyy - uy);
+            Px0 = Py0 = T(2) / T(3);
+            Pxp = Pxm = Pyp = Pym = T(1) / T(6);
+        }
+        // f^eq - s = drho P_a P_b + P_a (rho D_b) + (rho D_a)(P_b + D_b)
+        const T Ex0 = rho * Dx0, Exp = rho * Dxp, Exm = rho * Dxm;
+        const T Ey0 = rho * Dy0, Eyp = rho * Dyp, Eym = rho * Dym;
+        const T Hy0 = Py0 + Dy0, Hyp = Pyp + Dyp, Hym = Pym + Dym;
+#define LBM_GEQ(Pa, Ea, Pb, Eb, Hb) (((Pa) * (Pb)) * drho + (Pa) * (Eb) + (Ea) * (Hb))
+        geq[0] = LBM_GEQ(Px0, Ex0, Py0, Ey0, Hy0);
+        geq[1] = LBM_GEQ(Pxp, Exp, Py0, Ey0, Hy0);
+        geq[2] = LBM_GEQ(Px0, Ex0, Pyp, Eyp, Hyp);
+        geq[3] = LBM_GEQ(Pxm, Exm, Py0, Ey0, Hy0);
+        geq[4] = LBM_GEQ(Px0, Ex0, Pym, Eym, Hym);
+        geq[5] = LBM_GEQ(Pxp, Exp, Pyp, Eyp, Hyp);
+        geq[6] = LBM_GEQ(Pxm, Exm, Pyp, Eyp, Hyp);
+        geq[7] = LBM_GEQ(Pxm, Exm, Pym, Eym, Hym);
+        geq[8] = LBM_GEQ(Pxp, Exp, Pym, Eym, Hym);
 #undef LBM_GEQ
     } else {
-        // second-order equilibrium (Sec. 2, Hermite reading):
+        // second-order equilibrium (Sec. 2, Hermite reading), shift s = w rho0 (u_ref = 0):
         // f^eq_i = w_i rho (1 + 3 xi.u + 4.5 (xi.u)^2 - 1.5 u^2)
         const T usq = T(1.5) * (uxx + uyy);
 #pragma unroll
@@ -188,9 +244,21 @@ __device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], T w, T w3, T
     for (int i = 0; i < 9; ++i) fn[i] = g[i] - geq[i];
 
     if (MODEL == BGK) {
-        const T c = T(1) - w;
+        // f^neq has no mass or momentum in exact arithmetic; in finite precision it carries
+        // their rounding, which f* = f^eq + (1 - omega) f^neq would feed back with a factor
+        // |1 - omega| ~ 1 at low viscosity.  Remove it (the moment-space models drop the same
+        // components), i.e. subtract the populations (e0, ex/2, -ex/2, ey/2, -ey/2) that carry
+        // exactly those moments and nothing else: the map is unchanged, its FP32 rounding is
+        // that of the moment-space models.
+        const T e0 = ((fn[0] + fn[1]) + (fn[2] + fn[3])) + ((fn[4] + fn[5]) + (fn[6] + fn[7])) + fn[8];
+        const T hx = T(0.5) * ((fn[1] - fn[3]) + ((fn[5] - fn[7]) + (fn[8] - fn[6])));
+        const T hy = T(0.5) * ((fn[2] - fn[4]) + ((fn[5] - fn[7]) + (fn[6] - fn[8])));
+        fn[0] -= e0;
+        fn[1] -= hx; fn[3] += hx;
+        fn[2] -= hy; fn[4] += hy;
+        const T cc = T(1) - w;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) o[i] = geq[i] + c * fn[i];
+        for (int i = 0; i < 9; ++i) o[i] = geq[i] + cc * fn[i];
         return;
     }
 
@@ -267,78 +335,177 @@ __device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], T w, T w3, T
     o[8] = geq[8] + q * ((M22 - M11) + (M12 - M21));
 }
 
+// Per-thread FP64 accumulators of the blow-up diagnostics (used by the batched sweep).
+struct Diag {
+    double pert;      // sum |u - u_ref|^2
+    double ke;        // sum |u|^2
+    double rho_min;   // min rho
+    double nonfinite; // count of nodes with a non-finite rho or u
+};
+
 // ---------------------------------------------------------------------------------------
-// Fused pull step: gather (periodic) -> collide -> store, one thread per VEC consecutive
-// x-nodes of one row.  Loads and stores are aligned 16-byte vectors; the x-shifted planes
-// take their edge element from the neighbouring lane with a warp shuffle, or with one scalar
-// load at warp and row edges (where the periodic wrap is applied).  Warps walk the lattice
-// with a grid-stride loop (the grid is sized to the resident CTAs of the GPU).
-template <int MODEL, int EQ, typename S>
+// Gather of the nine planes of one vector segment (VEC consecutive x-nodes of row y) at the
+// periodic offsets -SIGN * xi_i: SIGN = +1 gives the populations that node x collides,
+// f_i(x) = A_i(x - xi_i) (pull); SIGN = -1 gives lambda_i(x + xi_i) (reverse streaming of the
+// adjoint).  All 32 lanes call it together with consecutive segments; loads are aligned
+// vectors, the x-shifted element comes from the neighbouring lane by a warp shuffle, or from
+// one scalar load at warp and row edges (where the periodic wrap is applied).
+template <typename S, int VEC, int SIGN>
+__device__ __forceinline__ void gather_pull(const S* __restrict__ src, int nx, int ny, int pitch, long long plane,
+                                            int y, int seg, int nseg, int x0, int nvalid, int lane,
+                                            typename Conv<S>::T (&f)[9][VEC]) {
+    using T = typename Conv<S>::T;
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y == ny - 1) ? 0 : y + 1;
+    const bool left_from_lane = (lane > 0) && (seg > 0);
+    const bool right_from_lane = (lane < 31) && (seg < nseg - 1);
+    const int xl = (x0 == 0) ? nx - 1 : x0 - 1;           // source of an x-offset of -1 at j = 0
+    const int xr = (x0 + nvalid >= nx) ? 0 : x0 + VEC;     // source of an x-offset of +1 at j = nvalid-1
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ex = SIGN * ex_of(i), ey = SIGN * ey_of(i);
+        const int row = (ey == 1) ? ym : ((ey == -1) ? yp : y);
+        const S* p = src + (long long)i * plane + (long long)row * pitch;
+        T v[VEC];
+        vload<S, VEC>(p + x0, v);
+        if (ex == 0) {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) f[i][j] = v[j];
+        } else if (ex == 1) {
+            T left = __shfl_up_sync(0xffffffffu, v[VEC - 1], 1);
+            if (!left_from_lane) left = Conv<S>::to_T(p[xl]);
+            f[i][0] = left;
+#pragma unroll
+            for (int j = 1; j < VEC; ++j) f[i][j] = v[j - 1];
+        } else {
+            T right = __shfl_down_sync(0xffffffffu, v[0], 1);
+            if (!right_from_lane) right = Conv<S>::to_T(p[xr]);
+#pragma unroll
+            for (int j = 0; j < VEC - 1; ++j) f[i][j] = (j + 1 < nvalid) ? v[j + 1] : right;
+            f[i][VEC - 1] = right;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// One pull step of one vector segment (VEC consecutive x-nodes of one row): gather
+// (periodic) -> collide -> store.  All 32 lanes of the warp call it together with
+// consecutive segment indices s = base + lane (base a multiple of 32); lanes with s >= total
+// take part in the shuffles and store nothing.
+template <int MODEL, int EQ, typename S, int VEC, bool DIAG, bool SHIFT>
+__device__ __forceinline__ void step_segment(const S* __restrict__ src, S* __restrict__ dst, const StepArgs& a,
+                                             const Consts<typename Conv<S>::T>& c, unsigned s, unsigned total,
+                                             int lane, Diag& dg) {
+    using T = typename Conv<S>::T;
+    const bool active = s < total;
+    const unsigned sc = active ? s : total - 1;
+    const int y = (int)(sc / (unsigned)a.nseg);
+    const int seg = (int)(sc - (unsigned)y * (unsigned)a.nseg);
+    const int x0 = seg * VEC;
+    const int nvalid = min(VEC, a.nx - x0);
+    T f[9][VEC];
+    gather_pull<S, VEC, 1>(src, a.nx, a.ny, a.pitch, a.plane, y, seg, a.nseg, x0, nvalid, lane, f);
+
+    T out[9][VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        T gin[9], gout[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) gin[i] = f[i][j];
+        T rho, ux, uy;
+        collide<MODEL, EQ, T, SHIFT>(gin, gout, c, rho, ux, uy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[i][j] = gout[i];
+        if (DIAG) {
+            if (active && j < nvalid) {
+                if (isfinite(rho) && isfinite(ux) && isfinite(uy)) {
+                    const T wx = ux - c.urx, wy = uy - c.ury;
+                    dg.pert += (double)(wx * wx + wy * wy);
+                    dg.ke += (double)(ux * ux + uy * uy);
+                    dg.rho_min = fmin(dg.rho_min, (double)rho);
+                } else {
+                    dg.nonfinite += 1.0;
+                }
+            }
+        }
+    }
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) vstore<S, VEC>(dst + (long long)i * a.plane + (long long)y * a.pitch + x0, out[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Single-lattice step: warps walk the lattice with a grid-stride loop (the grid is sized to
+// the resident CTAs of the GPU).
+template <int MODEL, int EQ, typename S, bool SHIFT>
 __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ src, S* __restrict__ dst, StepArgs a) {
-    using St = Store<S>;
-    using T = typename St::T;
-    constexpr int VEC = St::VEC;
+    using T = typename Conv<S>::T;
+    constexpr int VEC = DefaultVec<S>::value;
     const int lane = threadIdx.x & 31;
     const unsigned total = (unsigned)a.ny * (unsigned)a.nseg;
     const unsigned stride = gridDim.x * blockDim.x;
-    const T w = (T)a.w_nu, w3 = (T)a.w3, w4 = (T)a.w4, rho0 = (T)a.rho0;
+    const Consts<T> c = make_consts<T>(a);
+    Diag dg;
+    for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride)
+        step_segment<MODEL, EQ, S, VEC, false, SHIFT>(src, dst, a, c, base + lane, total, lane, dg);
+}
 
-    for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
-        const unsigned s = base + lane;
-        const bool active = s < total;
-        const unsigned sc = active ? s : total - 1;
-        const int y = (int)(sc / (unsigned)a.nseg);
-        const int seg = (int)(sc - (unsigned)y * (unsigned)a.nseg);
-        const int x0 = seg * VEC;
-        const int nvalid = min(VEC, a.nx - x0);
-        const int ym = (y == 0) ? a.ny - 1 : y - 1;
-        const int yp = (y == a.ny - 1) ? 0 : y + 1;
-        const bool left_from_lane = (lane > 0) && (seg > 0);
-        const bool right_from_lane = (lane < 31) && (seg < a.nseg - 1);
-        const int xl = (x0 == 0) ? a.nx - 1 : x0 - 1;           // source of xi_x = +1 at j = 0
-        const int xr = (x0 + nvalid >= a.nx) ? 0 : x0 + VEC;     // source of xi_x = -1 at j = nvalid-1
+// ---------------------------------------------------------------------------------------
+// Multi-lattice step: one launch advances every lattice of a group by one time step.  The
+// lattices' segment ranges, each padded to a multiple of 32, are concatenated; a warp finds
+// its lattice from the warp-aligned base index and runs that lattice's collision model.
+// One launch per time step instead of one per lattice removes the per-launch ramp and the
+// gaps between graph nodes that dominate small (<= 1024^2) lattices.
+constexpr int kGroupMax = 16;
 
-        T f[9][VEC];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int ex = ex_of(i), ey = ey_of(i);
-            const int row = (ey == 1) ? ym : ((ey == -1) ? yp : y);
-            const S* p = src + (long long)i * a.plane + (long long)row * a.pitch;
-            T v[VEC];
-            St::load(p + x0, v);
-            if (ex == 0) {
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) f[i][j] = v[j];
-            } else if (ex == 1) {
-                T left = __shfl_up_sync(0xffffffffu, v[VEC - 1], 1);
-                if (!left_from_lane) left = St::load1(p + xl);
-                f[i][0] = left;
-#pragma unroll
-                for (int j = 1; j < VEC; ++j) f[i][j] = v[j - 1];
-            } else {
-                T right = __shfl_down_sync(0xffffffffu, v[0], 1);
-                if (!right_from_lane) right = St::load1(p + xr);
-#pragma unroll
-                for (int j = 0; j < VEC - 1; ++j) f[i][j] = (j + 1 < nvalid) ? v[j + 1] : right;
-                f[i][VEC - 1] = right;
-            }
-        }
+struct GroupEntry {
+    const void* src;    // buffers of the storage type of the launch
+    void* dst;
+    StepArgs a;
+    int model;          // lbm::Model
+    int eq_order;       // 4, or 2 (BGK only)
+    unsigned begin;     // first padded segment index of this lattice
+    unsigned total;     // ny * nseg (unpadded)
+};
+struct GroupArgs {
+    int n;
+    unsigned padded_total;
+    GroupEntry e[kGroupMax];
+};
 
-        T out[9][VEC];
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            T gin[9], gout[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) gin[i] = f[i][j];
-            collide<MODEL, EQ, T>(gin, gout, w, w3, w4, rho0);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) out[i][j] = gout[i];
-        }
-        if (active) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i)
-                St::store(dst + (long long)i * a.plane + (long long)y * a.pitch + x0, out[i]);
-        }
+template <typename S, bool SH>
+__device__ __forceinline__ void group_segment(const GroupEntry& e, unsigned local, int lane) {
+    using T = typename Conv<S>::T;
+    constexpr int VEC = DefaultVec<S>::value;
+    const Consts<T> c = make_consts<T>(e.a);
+    Diag dg;
+    const unsigned s = local + lane;
+    const S* src = static_cast<const S*>(e.src);
+    S* dst = static_cast<S*>(e.dst);
+    switch (e.model) {
+        case BGK:
+            if (e.eq_order == 2) step_segment<BGK, 2, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg);
+            else step_segment<BGK, 4, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg);
+            break;
+        case RM: step_segment<RM, 4, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg); break;
+        case HM: step_segment<HM, 4, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg); break;
+        case CM: step_segment<CM, 4, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg); break;
+        case CHM: step_segment<CHM, 4, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg); break;
+        case CUM: step_segment<CUM, 4, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg); break;
+        case PR: step_segment<PR, 4, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg); break;
+        default: step_segment<RR, 4, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg); break;
+    }
+}
+
+template <typename S, bool SHIFT>
+__global__ void __launch_bounds__(256) group_step_kernel(const __grid_constant__ GroupArgs g) {
+    const int lane = threadIdx.x & 31;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < g.padded_total; base += stride) {
+        int k = 0;
+        while (k + 1 < g.n && base >= g.e[k + 1].begin) ++k;
+        group_segment<S, SHIFT>(g.e[k], base - g.e[k].begin, lane);
     }
 }
 

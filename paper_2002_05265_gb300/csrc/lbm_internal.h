@@ -7,11 +7,23 @@ namespace lbm {
 
 struct StepArgs;
 
-// Step kernel entry for (storage, model, equilibrium order); nullptr if not instantiated.
-const void* step_kernel_f64(int model, int eq_order);
-const void* step_kernel_f32(int model, int eq_order);
-const void* step_kernel_f16(int model, int eq_order);
-const void* step_kernel_bf16(int model, int eq_order);
+// Step kernel entry for (storage, model, equilibrium order, non-default shift); nullptr if not
+// instantiated.
+const void* step_kernel_f64(int model, int eq_order, bool shifted);
+const void* step_kernel_f32(int model, int eq_order, bool shifted);
+const void* step_kernel_f16(int model, int eq_order, bool shifted);
+const void* step_kernel_bf16(int model, int eq_order, bool shifted);
+// Multi-lattice step kernel (group_step_kernel<S>, one GroupArgs parameter) per storage.
+const void* group_kernel_f64(bool shifted);
+const void* group_kernel_f32(bool shifted);
+const void* group_kernel_f16(bool shifted);
+const void* group_kernel_bf16(bool shifted);
+
+// Batched persistent sweep kernel for (vector width, CTA size); nullptr if not instantiated.
+const void* batch_kernel_f64(int vec, int block);
+const void* batch_kernel_f32(int vec, int block);
+const void* batch_kernel_f16(int vec, int block);
+const void* batch_kernel_bf16(int vec, int block);
 
 // Vector width (nodes per thread) of the step kernel for a storage type.
 int storage_vec(int storage);
@@ -22,7 +34,8 @@ int storage_bytes(int storage);
 struct FieldArgs {
     int nx, ny, pitch;
     long long plane;
-    double rho0;
+    double rho0;         // shift s_i = rho0 phi(u_ref,x) phi(u_ref,y)
+    double urx, ury;
 };
 // f(x) = f^eq(rho(x), u(x)) (eq_order 2 or 4), scattered so the next pull gathers it.
 cudaError_t launch_init_eq(int storage, void* buf, const FieldArgs& a, int eq_order,
@@ -44,5 +57,30 @@ int reduce_blocks();
 cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, double* partials,
                           double* out8, int* status, long long* blowup_step, const CheckArgs& c,
                           cudaStream_t s);
+
+// Discrete adjoint (lbm_adjoint.cu).
+struct AdjArgs {
+    int nx, ny, pitch, nseg;
+    long long plane;
+    double w_nu, w3, w4, rho0;
+    double urx, ury;     // storage shift velocity
+};
+struct AdjointPlan {
+    int storage;            // LBM_F64 or LBM_F32 (lambda kept in the collision precision)
+    AdjArgs a;
+    const void* step_fwd;   // forward step kernel (src, dst, StepArgs), default shift
+    const void* step_adj;   // adjoint step kernel of the model
+    int grid_fwd, grid_adj, block;
+};
+int adjoint_plan(int storage, int model, int nx, int ny, int pitch, long long plane, double w, double w3, double w4,
+                 double rho0, double urx, double ury, AdjointPlan* p);
+cudaError_t adjoint_launch_fwd(const AdjointPlan& p, const StepArgs& sa, const void* src, void* dst, cudaStream_t s);
+cudaError_t adjoint_launch_step(const AdjointPlan& p, const void* state, const void* lam_in, void* lam_out,
+                                double* rate_part, cudaStream_t s);
+int adjoint_seed_blocks();
+cudaError_t adjoint_launch_seed(const AdjointPlan& p, const void* state, int loss, const double* uxt,
+                                const double* uyt, void* lam, double* loss_part, cudaStream_t s);
+cudaError_t adjoint_launch_init(const AdjointPlan& p, const void* state0, const void* lam, double* gux, double* guy,
+                                cudaStream_t s);
 
 }  // namespace lbm

@@ -3,5 +3,8 @@
 #include "lbm_internal.h"
 
 namespace lbm {
-const void* step_kernel_f16(int model, int eq_order) { return step_kernel_table<__half>(model, eq_order); }
+const void* step_kernel_f16(int model, int eq_order, bool shifted) {
+    return step_kernel_table<__half>(model, eq_order, shifted);
+}
+const void* group_kernel_f16(bool shifted) { return group_kernel_table<__half>(shifted); }
 }  // namespace lbm

@@ -3,5 +3,8 @@
 #include "lbm_internal.h"
 
 namespace lbm {
-const void* step_kernel_f64(int model, int eq_order) { return step_kernel_table<double>(model, eq_order); }
+const void* step_kernel_f64(int model, int eq_order, bool shifted) {
+    return step_kernel_table<double>(model, eq_order, shifted);
+}
+const void* group_kernel_f64(bool shifted) { return group_kernel_table<double>(shifted); }
 }  // namespace lbm

@@ -82,6 +82,25 @@ def shear_wave(nx, ny=None, amp=1e-4, mode=1, u0=0.0, rho0=1.0):
     return rho, ux, uy
 
 
+def smooth_random_field(nx, ny, kmax, seed):
+    """Random smooth periodic field: Fourier modes with |k_x|, |k_y| <= kmax and N(0, 1)
+    amplitudes, normalised to unit root-mean-square (seeded Philox)."""
+    g = _rng(seed)
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    out = np.zeros((ny, nx))
+    for kx in range(-kmax, kmax + 1):
+        for ky in range(0, kmax + 1):
+            a, b = g.normal(size=2)
+            ph = 2.0 * np.pi * (kx * x / nx + ky * y / ny)
+            out += a * np.cos(ph) + b * np.sin(ph)
+    return out / np.sqrt((out ** 2).mean())
+
+
+def gaussian_noise(shape, sigma, seed):
+    """N(0, sigma^2) array of the given shape (seeded Philox)."""
+    return _rng(seed).normal(0.0, sigma, size=shape)
+
+
 def random_populations_perturbation(shape, amp, seed):
     """U(-amp, amp) array of the given shape (used to perturb a state off equilibrium)."""
     return _rng(seed).uniform(-amp, amp, size=shape)

@@ -32,6 +32,12 @@ class lbm_rates(ctypes.Structure):
         return (self.omega_nu, self.omega3, self.omega4)
 
 
+class lbm_instance_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("model", ctypes.c_int), ("rates", lbm_rates),
+                ("ux_ref", ctypes.c_double), ("uy_ref", ctypes.c_double),
+                ("ke_ref", ctypes.c_double), ("ke_factor", ctypes.c_double)]
+
+
 class LBMError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"liblbm error {code}: {msg}")
@@ -64,7 +70,20 @@ _SIGNATURES = {
     "lbm_group_step": (_I, [_P, _LL]),
     "lbm_group_destroy": (None, [_P]),
     "lbm_group_set_timing": (_I, [_P, _I]),
-    "lbm_group_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_LL)]),
+    "lbm_group_timing": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
+    "lbm_set_shift_velocity": (_I, [_P, _D, _D]),
+    "lbm_adjoint_run": (_I, [_P, _LL, _I, _P, _P, _I, _P, _P, _P, _P, _P]),
+    "lbm_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(lbm_instance_desc), _I, _D, _P]),
+    "lbm_batch_destroy": (None, [_P]),
+    "lbm_batch_nodes": (_LL, [_P]),
+    "lbm_batch_init_equilibrium": (_I, [_P, _P, _P, _P]),
+    "lbm_batch_run": (_I, [_P, _LL, _I, _D]),
+    "lbm_batch_status": (_I, [_P, _P, _P, _P, _P]),
+    "lbm_batch_get_populations": (_I, [_P, _I, _P]),
+    "lbm_batch_set_shape": (_I, [_P, _I, _I]),
+    "lbm_batch_get_shape": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "lbm_batch_autotune": (_I, [_P, _LL, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_error_string": (ctypes.c_char_p, [_I]),
     "lbm_version": (ctypes.c_char_p, []),
@@ -214,9 +233,99 @@ def lbm_group_set_timing(group, enable=True):
 
 
 def lbm_group_timing(group):
-    ms, n = _D(), _LL()
-    _check(load_library().lbm_group_timing(group, ctypes.byref(ms), ctypes.byref(n)))
-    return ms.value, n.value
+    """(summed replay ms, lattice time steps, step-kernel launches) of the timed replays."""
+    ms, n, k = _D(), _LL(), _LL()
+    _check(load_library().lbm_group_timing(group, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)))
+    return ms.value, n.value, k.value
+
+
+def lbm_set_shift_velocity(ctx, ux_ref, uy_ref):
+    _check(load_library().lbm_set_shift_velocity(ctx, ux_ref, uy_ref), ctx)
+
+
+def lbm_adjoint_run(ctx, nsteps, loss, ux_target, uy_target, grad_ux0, grad_uy0, checkpoint_every=0):
+    """Runs N steps forward with checkpoints and the discrete adjoint backwards; fills
+    grad_ux0 / grad_uy0 and returns (loss, [dL/domega_nu, dL/domega3, dL/domega4],
+    (forward_ms, backward_ms))."""
+    import numpy as np
+    gr = np.zeros(3)
+    L = np.zeros(1)
+    t = np.zeros(2)
+    _check(load_library().lbm_adjoint_run(ctx, nsteps, loss, _addr(ux_target), _addr(uy_target), checkpoint_every,
+                                          _addr(grad_ux0), _addr(grad_uy0), gr.ctypes.data, L.ctypes.data,
+                                          t.ctypes.data), ctx)
+    return float(L[0]), gr, (float(t[0]), float(t[1]))
+
+
+def _bcheck(rc, b=None):
+    if rc != LBM_OK:
+        lib = load_library()
+        msg = lib.lbm_batch_last_error(b).decode() if b else lib.lbm_error_string(rc).decode()
+        raise LBMError(rc, msg or lib.lbm_error_string(rc).decode())
+
+
+def lbm_batch_create(descs, storage=LBM_F32, rho0=1.0, stream=None):
+    """descs: sequence of dicts with nx, ny, model, rates (3-tuple or lbm_rates), ux_ref,
+    uy_ref and optional ke_ref, ke_factor."""
+    if isinstance(storage, str):
+        storage = STORAGES[storage]
+    arr = (lbm_instance_desc * len(descs))()
+    for k, d in enumerate(descs):
+        r = d["rates"] if isinstance(d["rates"], lbm_rates) else lbm_rates(*d["rates"])
+        m = d["model"] if not isinstance(d["model"], str) else MODELS[d["model"]]
+        arr[k] = lbm_instance_desc(d["nx"], d["ny"], m, r, d.get("ux_ref", 0.0), d.get("uy_ref", 0.0),
+                                   d.get("ke_ref", 0.0), d.get("ke_factor", 1.0))
+    h = _P()
+    _bcheck(load_library().lbm_batch_create(ctypes.byref(h), len(descs), arr, storage, rho0, _stream(stream)))
+    return h.value
+
+
+def lbm_batch_destroy(b):
+    load_library().lbm_batch_destroy(b)
+
+
+def lbm_batch_nodes(b):
+    return load_library().lbm_batch_nodes(b)
+
+
+def lbm_batch_init_equilibrium(b, rho, ux, uy):
+    _bcheck(load_library().lbm_batch_init_equilibrium(b, _addr(rho), _addr(ux), _addr(uy)), b)
+
+
+def lbm_batch_run(b, target_steps, check_every=100, growth=1e4):
+    _bcheck(load_library().lbm_batch_run(b, target_steps, check_every, growth), b)
+
+
+def lbm_batch_status(b, n):
+    """(status[n], blowup_step[n], steps[n], diag[n, 4]) as numpy arrays."""
+    import numpy as np
+    st = np.zeros(n, dtype=np.int32)
+    bs = np.zeros(n, dtype=np.int64)
+    steps = np.zeros(n, dtype=np.int64)
+    diag = np.zeros((n, 4))
+    _bcheck(load_library().lbm_batch_status(b, st.ctypes.data, bs.ctypes.data, steps.ctypes.data, diag.ctypes.data), b)
+    return st, bs, steps, diag
+
+
+def lbm_batch_get_populations(b, index, f):
+    _bcheck(load_library().lbm_batch_get_populations(b, index, _addr(f)), b)
+
+
+def lbm_batch_set_shape(b, vec, block):
+    _bcheck(load_library().lbm_batch_set_shape(b, vec, block), b)
+
+
+def lbm_batch_get_shape(b):
+    v, k, g = _I(), _I(), _I()
+    _bcheck(load_library().lbm_batch_get_shape(b, ctypes.byref(v), ctypes.byref(k), ctypes.byref(g)), b)
+    return v.value, k.value, g.value
+
+
+def lbm_batch_autotune(b, trial_steps=200, check_every=100):
+    v, k, ms = _I(), _I(), _D()
+    _bcheck(load_library().lbm_batch_autotune(b, trial_steps, check_every, ctypes.byref(v), ctypes.byref(k),
+                                              ctypes.byref(ms)), b)
+    return v.value, k.value, ms.value
 
 
 def lbm_version():
@@ -270,3 +379,6 @@ class Lattice:
 
     def set_rates(self, rates):
         lbm_set_rates(self.ctx, rates)
+
+    def set_shift_velocity(self, ux_ref, uy_ref):
+        lbm_set_shift_velocity(self.ctx, ux_ref, uy_ref)

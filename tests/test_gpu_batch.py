@@ -1,0 +1,157 @@
+"""GPU tests of the batched stability sweep (one persistent launch over many lattices of
+uneven size, each with its own model, rates and blow-up detection), against the oracle."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2002_05265_gb300 import flows  # noqa: E402
+import oracle.lbm as olbm  # noqa: E402
+from oracle.collision import macroscopic  # noqa: E402
+
+MODELS = ["bgk", "rm", "hm", "cm", "chm", "k", "pr", "rr"]
+CS = 1.0 / np.sqrt(3.0)
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_05265_gb300 import build, lbm
+    build.build_library()
+    lbm.load_library()
+    return lbm
+
+
+def _instances(n, seed=0, sizes=(33, 72), ma=(0.0, 0.4), nu=(1e-4, 1e-2)):
+    """Uneven lattices, models and presets cycling, Ma uniform, nu log-uniform, uniform flow
+    along +x plus 1e-6 velocity noise (the perturbed uniform flows of the stability study)."""
+    g = np.random.default_rng(seed)
+    descs, fields = [], []
+    for k in range(n):
+        nx, ny = (int(v) for v in g.integers(sizes[0], sizes[1] + 1, 2))
+        model = MODELS[k % len(MODELS)]
+        preset = "srt" if (k // len(MODELS)) % 2 == 0 else "reg"
+        Ma = float(g.uniform(*ma))
+        nuv = float(np.exp(g.uniform(np.log(nu[0]), np.log(nu[1]))))
+        rates = olbm.rates_from_nu(nuv, preset)
+        descs.append(dict(nx=nx, ny=ny, model=model, rates=rates, ux_ref=Ma * CS, uy_ref=0.0))
+        fields.append(flows.uniform_noise(nx, ny, Ma=Ma, amp=1e-6, seed=1000 + k))
+    return descs, fields
+
+
+def _concat(fields):
+    return [np.ascontiguousarray(np.concatenate([f[i].ravel() for f in fields])) for i in range(3)]
+
+
+def _batch(L, descs, fields, storage):
+    b = L.lbm_batch_create(descs, storage=storage)
+    rho, ux, uy = _concat(fields)
+    L.lbm_batch_init_equilibrium(b, rho, ux, uy)
+    return b
+
+
+def test_batch_fp64_matches_oracle_per_instance(L):
+    """16 instances (every model, SRT and REG), FP64: each instance's populations after 200
+    steps within 1e-12 relative of the oracle."""
+    descs, fields = _instances(16, seed=1)
+    b = _batch(L, descs, fields, L.LBM_F64)
+    L.lbm_batch_run(b, 200, check_every=50)
+    st, bs, steps, _ = L.lbm_batch_status(b, len(descs))
+    assert (st == 0).all() and (steps == 200).all()
+    for k, (d, f) in enumerate(zip(descs, fields)):
+        got = np.empty((9, d["ny"], d["nx"]))
+        L.lbm_batch_get_populations(b, k, got)
+        ref = olbm.run(olbm.init_equilibrium(*f), d["model"], d["rates"], 200)
+        assert float(np.max(np.abs(got - ref) / np.abs(ref))) <= 1e-12, (k, d["model"])
+    L.lbm_batch_destroy(b)
+
+
+def test_batch_fp32_matches_oracle_and_chunked_runs(L):
+    """FP32 velocity within 1e-5 of the oracle after 300 steps; running to 120 then 300 steps
+    gives the same bits as running to 300 at once."""
+    descs, fields = _instances(10, seed=2)
+    a = _batch(L, descs, fields, L.LBM_F32)
+    b = _batch(L, descs, fields, L.LBM_F32)
+    L.lbm_batch_run(a, 300, check_every=100)
+    L.lbm_batch_run(b, 120, check_every=100)
+    L.lbm_batch_run(b, 300, check_every=100)
+    for k, (d, f) in enumerate(zip(descs, fields)):
+        ga = np.empty((9, d["ny"], d["nx"]))
+        gb = np.empty_like(ga)
+        L.lbm_batch_get_populations(a, k, ga)
+        L.lbm_batch_get_populations(b, k, gb)
+        np.testing.assert_array_equal(ga, gb)
+        ref = olbm.run(olbm.init_equilibrium(*f), d["model"], d["rates"], 300)
+        _, gx, gy = macroscopic(ga)
+        _, rx, ry = macroscopic(ref)
+        assert max(np.abs(gx - rx).max(), np.abs(gy - ry).max()) <= 1e-5, (k, d["model"])
+    L.lbm_batch_destroy(a)
+    L.lbm_batch_destroy(b)
+
+
+def test_batch_blowup_detection_per_instance(L):
+    """Unstable instances (BGK at Ma = 0.9, nu = 1e-6) are flagged at a check step and stop;
+    stable neighbours in the same launch run to the target untouched."""
+    descs, fields = _instances(6, seed=3, ma=(0.05, 0.2), nu=(1e-3, 1e-2))
+    for k in (1, 4):
+        nx, ny = descs[k]["nx"], descs[k]["ny"]
+        descs[k] = dict(nx=nx, ny=ny, model="bgk", rates=olbm.rates_from_nu(1e-6), ux_ref=0.9 * CS, uy_ref=0.0)
+        fields[k] = flows.uniform_noise(nx, ny, Ma=0.9, amp=1e-6, seed=77 + k)
+    b = _batch(L, descs, fields, L.LBM_F32)
+    L.lbm_batch_run(b, 3000, check_every=100, growth=1e4)
+    st, bs, steps, diag = L.lbm_batch_status(b, len(descs))
+    for k in range(len(descs)):
+        if k in (1, 4):
+            assert st[k] == L.LBM_ERR_BLOWUP and bs[k] % 100 == 0 and 0 < bs[k] < 3000 and steps[k] == bs[k] + 1
+        else:
+            assert st[k] == 0 and bs[k] == -1 and steps[k] == 3000
+            assert diag[k, 0] < 1e4 * diag[k, 3]
+    L.lbm_batch_destroy(b)
+
+
+def test_batch_autotune_keeps_state_and_results(L):
+    descs, fields = _instances(24, seed=4)
+    b = _batch(L, descs, fields, L.LBM_F32)
+    ref = _batch(L, descs, fields, L.LBM_F32)
+    vec, block, ms = L.lbm_batch_autotune(b, trial_steps=50, check_every=25)
+    assert vec in (2, 4) and block in (128, 256, 512) and ms > 0
+    assert L.lbm_batch_get_shape(b)[:2] == (vec, block)
+    st, bs, steps, _ = L.lbm_batch_status(b, len(descs))
+    assert (steps == 0).all()                       # trials restored the initial state
+    L.lbm_batch_run(b, 100, check_every=25)
+    L.lbm_batch_run(ref, 100, check_every=25)
+    for k, d in enumerate(descs):
+        ga = np.empty((9, d["ny"], d["nx"]))
+        gb = np.empty_like(ga)
+        L.lbm_batch_get_populations(b, k, ga)
+        L.lbm_batch_get_populations(ref, k, gb)
+        np.testing.assert_allclose(ga, gb, rtol=1e-6, atol=1e-7)
+    L.lbm_batch_destroy(b)
+    L.lbm_batch_destroy(ref)
+
+
+def test_batch_fp16_instances(L):
+    """FP16 storage with the per-instance mean-flow shift: velocity within 1e-4 of the oracle
+    after 300 steps of perturbed uniform flows."""
+    descs, fields = _instances(8, seed=5)
+    b = _batch(L, descs, fields, L.LBM_F16)
+    L.lbm_batch_run(b, 300, check_every=100)
+    for k, (d, f) in enumerate(zip(descs, fields)):
+        got = np.empty((9, d["ny"], d["nx"]))
+        L.lbm_batch_get_populations(b, k, got)
+        ref = olbm.run(olbm.init_equilibrium(*f), d["model"], d["rates"], 300)
+        _, gx, gy = macroscopic(got)
+        _, rx, ry = macroscopic(ref)
+        assert max(np.abs(gx - rx).max(), np.abs(gy - ry).max()) <= 1e-4, (k, d["model"])
+    L.lbm_batch_destroy(b)
+
+
+def test_batch_rejects_bad_descriptors(L):
+    with pytest.raises(L.LBMError):
+        L.lbm_batch_create([dict(nx=2, ny=40, model="bgk", rates=(1.5, 1.5, 1.5))])
+    with pytest.raises(L.LBMError):
+        L.lbm_batch_create([dict(nx=40, ny=40, model="bgk", rates=(2.5, 1.5, 1.5))])
