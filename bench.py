@@ -62,7 +62,14 @@ def parse():
     p.add_argument("--sweep", default=None,
                    help="instead of the benchmark step, time single lattices: MODELS:STORAGES:SIZE, e.g. "
                         "all:f32,f16,bf16:16384 (one JSON line per combination)")
+    p.add_argument("--path", default="auto", choices=["auto", "vector", "bulk"],
+                   help="step-kernel family: copy-engine staged (bulk), register-staged (vector), or the "
+                        "library's choice (auto: bulk where the row length allows it)")
+    p.add_argument("--stages", type=int, default=0, help="shared-memory stages of the bulk-copy kernel (0 = default)")
     return p.parse_args()
+
+
+PATHS = {"auto": 0, "vector": 1, "bulk": 2}
 
 
 def dist_setup(args):
@@ -160,18 +167,24 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def source_hashes(names):
+    """sha256 of kernel source files of csrc/ (the ncu figures are valid only for these)."""
+    import hashlib
+    out = {}
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2002_05265_gb300", "csrc", n), "rb") as fh:
+            out[n] = hashlib.sha256(fh.read()).hexdigest()
+    return out
+
+
 def ncu_traffic(kernel_tag):
     """Per-launch DRAM bytes of the step kernel from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path))
-    import hashlib
-    src = os.path.join(ROOT, "paper_2002_05265_gb300", "csrc", "lbm_device.cuh")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    e = d.get(kernel_tag)
-    if not e or d.get("kernel_source_sha256") != h:
+    e = json.load(open(path)).get(kernel_tag)
+    if not e or e.get("sources") != source_hashes(sorted(e.get("sources", {}))):
         return None
     return e.get("dram_bytes_per_launch_full_size")
 
@@ -296,7 +309,8 @@ def run_accuracy(args):
             rx, ry = velocity(m, "f64", False, w)
             ok = bool(torch.isfinite(rx).all() and torch.isfinite(ry).all())
             norm = torch.sqrt((rx * rx + ry * ry).sum())
-            for storage, shift in (("f32", False), ("f16", False), ("bf16", False), ("f16", True), ("bf16", True)):
+            for storage, shift in (("f32", False), ("f16", False), ("bf16", False), ("f32", True), ("f16", True),
+                                   ("bf16", True)):
                 gx, gy = velocity(m, storage, shift, w)
                 err = float(torch.sqrt(((gx - rx) ** 2 + (gy - ry) ** 2).sum()) / norm) if ok else None
                 print(json.dumps({"accuracy": True, "nu": nu, "model": m, "storage": storage,
@@ -323,6 +337,7 @@ def run_sweep(args):
         for m in models:
             rates = lbm.lbm_rates_from_nu(1e-6, lbm.LBM_PRESET_SRT if _preset(m) == "srt" else lbm.LBM_PRESET_REG)
             lat = lbm.Lattice(n, n, lbm.MODELS[m], rates, storage=lbm.STORAGES[s], stream=stream)
+            lat.set_kernel_path(PATHS[args.path], args.stages)
             lat.init_equilibrium(*fields)
             g = lbm.lbm_group_create([lat.ctx], graph_steps=2)
             lbm.lbm_group_step(g, max(2, args.warmup - args.warmup % 2), lat.ctx)
@@ -330,7 +345,8 @@ def run_sweep(args):
             lbm.lbm_group_step(g, args.steps - args.steps % 2, lat.ctx)
             rms, nl, _ = lbm.lbm_group_timing(g)
             t = rms / 1e3 / nl
-            print(json.dumps({"sweep": True, "model": m, "storage": s, "lattice": f"{n}x{n}", "steps": nl,
+            print(json.dumps({"sweep": True, "model": m, "storage": s, "path": args.path, "stages": args.stages,
+                              "lattice": f"{n}x{n}", "steps": nl,
                               "glups": n * n / t / 1e9, "gbs": BYTES_PER_LU[s] * n * n / t / 1e9,
                               "ms_per_step": t * 1e3}), flush=True)
             lbm.lbm_group_destroy(g)
@@ -461,6 +477,7 @@ def main():
     for m in MODELS:
         rates = lbm.lbm_rates_from_nu(NU, lbm.LBM_PRESET_SRT if _preset(m) == "srt" else lbm.LBM_PRESET_REG)
         lat = lbm.Lattice(L, L, lbm.MODELS[m], rates, storage=lbm.LBM_F32, stream=stream)
+        lat.set_kernel_path(PATHS[args.path], args.stages)
         lat.set_check(CHECK_EVERY)
         lats.append(lat)
     group = lbm.lbm_group_create([x.ctx for x in lats], graph_steps=GRAPH_STEPS)
@@ -511,12 +528,14 @@ def main():
     avg_launch_s = replay_ms / 1e3 / kernel_launches
     bytes_per_launch = BYTES_PER_LU["f32"] * L * L * lattice_steps / kernel_launches
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    traffic = ncu_traffic("f32_group_8x1024")
+    bulk = args.path != "vector"   # 1024 * 4 B rows: the bulk-copy kernel unless told otherwise
+    traffic = ncu_traffic("f32_tile_8x1024" if bulk else "f32_group_8x1024")
+    kname = ("lbm::tile_step_kernel<float> (cp.async.bulk ring)" if bulk
+             else "lbm::group_step_kernel<float> (register-staged)")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind, "launch_us": avg_launch_s * 1e6,
                 "bytes_per_launch": bytes_per_launch,
-                "kernel": "lbm::group_step_kernel<float>: one launch = one time step of the 8 lattices, "
-                          "72 B per lattice update"}
+                "kernel": kname + ": one launch = one time step of the 8 lattices, 72 B per lattice update"}
 
     launches_per_step = S + len(MODELS) * (1 + 2 * (S // CHECK_EVERY) + 1)
 
@@ -542,6 +561,7 @@ def main():
         for m in MODELS:
             rates = lbm.lbm_rates_from_nu(NU, lbm.LBM_PRESET_SRT if _preset(m) == "srt" else lbm.LBM_PRESET_REG)
             big = lbm.Lattice(4096, 4096, lbm.MODELS[m], rates, storage=lbm.LBM_F32, stream=stream)
+            big.set_kernel_path(PATHS[args.path], args.stages)
             f4 = flows.double_shear_layer(4096, Ma=MA)
             big.init_equilibrium(*[torch.from_numpy(a).cuda() for a in f4])
             g1 = lbm.lbm_group_create([big.ctx], graph_steps=32)

@@ -173,7 +173,9 @@ int lbm_set_populations(lbm_ctx* ctx, const double* f);
 int lbm_set_check(lbm_ctx* ctx, long long every, double ke_ref, double ke_factor,
                   double uref_x, double uref_y);
 
-/* Wait for the context's stream, then report: *status = LBM_OK or LBM_ERR_BLOWUP,
+/* Wait for the context's stream, then report: *status = LBM_OK, LBM_ERR_BLOWUP, or
+ * LBM_ERR_TIMEOUT if a bulk-copy step kernel gave up waiting for its copies (a bounded wait
+ * of about two seconds; it then stops advancing the lattice),
  * *blowup_step = first checked step at which the criterion fired (-1 if none),
  * *steps = steps taken since the last init.  Any pointer may be NULL. */
 int lbm_status(lbm_ctx* ctx, int* status, long long* blowup_step, long long* steps);
@@ -184,6 +186,21 @@ int lbm_synchronize(lbm_ctx* ctx);
 /* Grid geometry actually used: row pitch in elements (>= nx, multiple of 32), CUDA grid and
  * block sizes of the step kernel. */
 int lbm_get_layout(const lbm_ctx* ctx, int* pitch, int* grid, int* block);
+
+/* Kernel family that advances a context (library design choice; the paper has no
+ * counterpart).  Both compute the same pull stream-and-collide of Eq. StreamCollide:
+ *   LBM_PATH_VECTOR  register-staged: each warp loads its nodes' nine pulled 16-byte vectors
+ *                    itself (x-shifted elements by warp shuffles); any nx.
+ *   LBM_PATH_BULK    copy-engine staged: cp.async.bulk copies each tile's nine pulled row
+ *                    segments into a ring of `stages` (2-4; 0 = default) shared-memory stages
+ *                    on mbarriers while eight consumer warps collide earlier tiles; needs
+ *                    nx * (bytes per population) to be a multiple of 16.
+ *   LBM_PATH_AUTO    BULK where the row length allows it, else VECTOR (the default).
+ * Applies to the context's next lbm_step and to groups created afterwards.  Errors:
+ * LBM_ERR_INVALID_ARG for an unknown path or stage count, LBM_ERR_UNSUPPORTED for BULK on a
+ * lattice whose rows are not a multiple of 16 bytes. */
+enum { LBM_PATH_AUTO = 0, LBM_PATH_VECTOR = 1, LBM_PATH_BULK = 2 };
+int lbm_set_kernel_path(lbm_ctx* ctx, int path, int stages);
 
 /* Several contexts advanced together, one time step of each in turn (so a set of lattices
  * whose sum exceeds L2 streams from HBM as a single large one would), captured in CUDA

@@ -39,6 +39,10 @@ template <typename S> struct AdjVec {
     static constexpr int value = DefaultVec<S>::value / LBM_ADJ_VEC_DIV > 0 ? DefaultVec<S>::value / LBM_ADJ_VEC_DIV : 1;
 };
 
+template <typename T> __device__ __forceinline__ const T* adj_consts(const AdjArgs& a);
+template <> __device__ __forceinline__ const float* adj_consts<float>(const AdjArgs& a) { return a.cf; }
+template <> __device__ __forceinline__ const double* adj_consts<double>(const AdjArgs& a) { return a.cd; }
+
 // One adjoint step: lam_out = J^T (reverse-streamed lam_in) at every node; the rate
 // sensitivities are accumulated into this block's FP64 slot of `rate_part` (3 per block).
 template <int MODEL, typename S>
@@ -52,10 +56,11 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_step_kernel(const S* __rest
     const int nseg = (a.nx + VEC - 1) / VEC;
     const unsigned total = (unsigned)a.ny * (unsigned)nseg;
     const unsigned stride = gridDim.x * blockDim.x;
-    const T w = (T)a.w_nu, w3 = (T)a.w3, w4 = (T)a.w4, rho0 = (T)a.rho0;
-    const T urx = (T)a.urx, ury = (T)a.ury;
-    const T Px[3] = {(T)phi1d(0, a.urx), (T)phi1d(1, a.urx), (T)phi1d(-1, a.urx)};
-    const T Py[3] = {(T)phi1d(0, a.ury), (T)phi1d(1, a.ury), (T)phi1d(-1, a.ury)};
+    // constants precomputed on the host in both precisions (no FP64 set-up in the kernel)
+    const T* ct = adj_consts<T>(a);
+    const T w = ct[0], w3 = ct[1], w4 = ct[2], rho0 = ct[3], urx = ct[4], ury = ct[5];
+    const T Px[3] = {ct[6], ct[7], ct[8]};
+    const T Py[3] = {ct[9], ct[10], ct[11]};
     // per-thread sums in the collision precision (a thread handles a few nodes), FP64 from
     // the block fold on
     T acc[3] = {T(0), T(0), T(0)};
@@ -92,13 +97,15 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_step_kernel(const S* __rest
                 vstore<T, VEC>(lam_out + (long long)i * a.plane + (long long)y * a.pitch + x0, out[i]);
         }
     }
+    // warp sums in the collision precision (32 per-thread sums of a few nodes), FP64 from the
+    // block fold on: GB300's FP64 pipe is narrow, per-thread FP64 work would dominate
     __shared__ double sh[kAdjBlock / 32][3];
     const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        double x = (double)acc[k];
+        T x = acc[k];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) sh[warp][k] = x;
+        if (lane == 0) sh[warp][k] = (double)x;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
@@ -216,6 +223,12 @@ int adjoint_plan(int storage, int model, int nx, int ny, int pitch, long long pl
     p->storage = storage;
     p->a.nx = nx; p->a.ny = ny; p->a.pitch = pitch; p->a.nseg = (nx + vec - 1) / vec; p->a.plane = plane;
     p->a.w_nu = w; p->a.w3 = w3; p->a.w4 = w4; p->a.rho0 = rho0; p->a.urx = urx; p->a.ury = ury;
+    {
+        StepArgs t{};
+        t.w_nu = w; t.w3 = w3; t.w4 = w4; t.rho0 = rho0; t.urx = urx; t.ury = ury;
+        fill_consts(t);
+        for (int k = 0; k < kNumConsts; ++k) { p->a.cd[k] = t.cd[k]; p->a.cf[k] = t.cf[k]; }
+    }
     const bool shifted = urx != 0.0 || ury != 0.0;
     p->step_adj = storage == LBM_F64 ? adjoint_kernel_for<double>(model) : adjoint_kernel_for<float>(model);
     p->step_fwd = storage == LBM_F64 ? step_kernel_f64(model, 4, shifted) : step_kernel_f32(model, 4, shifted);

@@ -13,6 +13,7 @@
 #include "lbm.h"
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_tile.cuh"
 
 using lbm::CheckArgs;
 using lbm::FieldArgs;
@@ -40,6 +41,8 @@ struct lbm_ctx {
     long long* blowup_step = nullptr;  // device
     long long check_every = 0;
     double ke_ref = 0.0, ke_factor = 1.0, uref_x = 0.0, uref_y = 0.0;
+    int path = LBM_PATH_AUTO;          // kernel family (lbm_set_kernel_path)
+    int stages = 0;                    // bulk-copy ring stages, 0 = default
     lbm_group* own_group = nullptr;    // used by lbm_step
     unsigned gen = 0;                  // bumped when kernel arguments change (graphs re-record)
     char err[512] = {0};
@@ -52,6 +55,12 @@ struct lbm_group {
     int ggrid[2] = {0, 0};
     std::vector<unsigned> begin;       // padded segment offsets of the contexts
     unsigned padded_total = 0;
+    int tiled = 0;                     // one bulk-copy staged launch per time step
+    const void* tkernel[2] = {nullptr, nullptr};   // default shift / reference-velocity shift
+    int tgrid[2] = {0, 0};
+    int tsmem = 0;                     // dynamic shared memory of the bulk-copy kernel
+    std::vector<unsigned> tbegin;      // first tile of each context
+    unsigned ttotal = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;
     int graph_steps = 0;
@@ -137,6 +146,7 @@ StepArgs step_args(const lbm_ctx* c) {
     a.rho0 = c->rho0;
     a.urx = c->urx;
     a.ury = c->ury;
+    lbm::fill_consts(a);
     return a;
 }
 
@@ -156,6 +166,42 @@ const void* pick_group_kernel(int storage, bool shifted) {
         default: return nullptr;
     }
 }
+
+// rows of a whole number of 16-byte chunks: every bulk copy of the tile kernel is aligned
+bool row_aligned(const lbm_ctx* c) { return ((long long)c->nx * lbm::storage_bytes(c->storage)) % 16 == 0; }
+
+const void* pick_tile_kernel(int storage, bool shifted, int stages) {
+    switch (storage) {
+        case LBM_F64: return lbm::tile_kernel_f64(shifted, stages);
+        case LBM_F32: return lbm::tile_kernel_f32(shifted, stages);
+        case LBM_F16: return lbm::tile_kernel_f16(shifted, stages);
+        case LBM_BF16: return lbm::tile_kernel_bf16(shifted, stages);
+        default: return nullptr;
+    }
+}
+int tile_width(int storage) {
+    switch (storage) {
+        case LBM_F64: return lbm::Tile<double>::W;
+        case LBM_F32: return lbm::Tile<float>::W;
+        default: return lbm::Tile<__half>::W;
+    }
+}
+int tile_smem(int storage, int stages) {
+    switch (storage) {
+        case LBM_F64: return lbm::tile_smem_bytes<double>(stages);
+        case LBM_F32: return lbm::tile_smem_bytes<float>(stages);
+        default: return lbm::tile_smem_bytes<__half>(stages);
+    }
+}
+// rows per row-block tile (>= 2), or 1 for row-segment tiles
+int tile_rows(const lbm_ctx* c, int W) { return 2 * c->nx <= W ? W / c->nx : 1; }
+unsigned tile_count(const lbm_ctx* c, int W) {
+    const int R = tile_rows(c, W);
+    if (R > 1) return (unsigned)((c->ny + R - 1) / R);
+    return (unsigned)c->ny * (unsigned)((c->nx + W - 1) / W);
+}
+// ring depth of the bulk-copy kernel when the caller chose none
+int default_stages(int) { return 2; }
 
 // true when p is device-accessible memory the kernels may read/write directly
 bool is_device_ptr(const void* p) {
@@ -217,7 +263,53 @@ int launch_group_once(lbm_group* g, cudaStream_t s, int sh) {
     return LBM_OK;
 }
 
+// bulk-copy staged launch of a tiled group: one time step of every context, from src[k] to
+// dst[k] (the contexts' own buffers, or the recomputation ring of the adjoint)
+cudaError_t launch_tile(lbm_group* g, const void* const* src, void* const* dst, cudaStream_t s, int sh) {
+    lbm::TileArgs ta;
+    ta.n = (int)g->ctx.size();
+    ta.total = g->ttotal;
+    ta.flag = g->ctx[0]->status + 1;   // second int of the first context's status word
+    const int W = tile_width(g->ctx[0]->storage);
+    for (size_t k = 0; k < g->ctx.size(); ++k) {
+        lbm_ctx* c = g->ctx[k];
+        lbm::TileEntry& e = ta.e[k];
+        e.src = src[k];
+        e.dst = dst[k];
+        e.a = step_args(c);
+        e.model = c->model;
+        e.eq_order = c->eq_order;
+        e.rows = tile_rows(c, W);
+        e.ntx = e.rows > 1 ? 0 : (c->nx + W - 1) / W;
+        e.begin = g->tbegin[k];
+    }
+    void* args[] = {(void*)&ta};
+    return cudaLaunchKernel(g->tkernel[sh], dim3(g->tgrid[sh]), dim3(lbm::kTileThreads), args, (size_t)g->tsmem, s);
+}
+
+// one time step of every context of a tiled group, as one bulk-copy staged launch
+int launch_tile_once(lbm_group* g, cudaStream_t s, int sh) {
+    std::vector<const void*> src(g->ctx.size());
+    std::vector<void*> dst(g->ctx.size());
+    for (size_t k = 0; k < g->ctx.size(); ++k) {
+        src[k] = g->ctx[k]->buf[g->ctx[k]->cur];
+        dst[k] = g->ctx[k]->buf[g->ctx[k]->cur ^ 1];
+    }
+    LBM_CK(g->ctx[0], launch_tile(g, src.data(), dst.data(), s, sh));
+    for (lbm_ctx* c : g->ctx) {
+        c->cur ^= 1;
+        c->steps += 1;
+    }
+    return LBM_OK;
+}
+
 int group_step_once(lbm_group* g, cudaStream_t s) {
+    if (g->tiled) {
+        int nsh = 0;
+        for (lbm_ctx* c : g->ctx) nsh += is_shifted(c) ? 1 : 0;
+        if (nsh == 0) return launch_tile_once(g, s, 0);
+        if (nsh == (int)g->ctx.size()) return launch_tile_once(g, s, 1);
+    }
     if (g->fused) {
         int nsh = 0;
         for (lbm_ctx* c : g->ctx) nsh += is_shifted(c) ? 1 : 0;
@@ -302,7 +394,7 @@ int group_replay(lbm_group* g) {
     if (g->timing) {
         LBM_CK(c0, cudaEventRecord(e1, g->stream));
         g->pending_lattice_steps += (long long)g->graph_steps * (long long)g->ctx.size();
-        g->pending_kernels += (long long)g->graph_steps * (g->fused ? 1LL : (long long)g->ctx.size());
+        g->pending_kernels += (long long)g->graph_steps * ((g->fused || g->tiled) ? 1LL : (long long)g->ctx.size());
     }
     for (lbm_ctx* c : g->ctx) c->steps += g->graph_steps;   // even: buffers end where they began
     return LBM_OK;
@@ -553,7 +645,8 @@ int lbm_status(lbm_ctx* c, int* status, long long* blowup_step, long long* steps
     long long h[2] = {0, -1};
     LBM_CK(c, cudaMemcpyAsync(h, c->status, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     LBM_CK(c, cudaStreamSynchronize(c->stream));
-    if (status) *status = (int)(h[0] & 0xffffffff);
+    const int timeout = (int)((unsigned long long)h[0] >> 32);   // set by a bulk-copy kernel's bounded wait
+    if (status) *status = timeout ? LBM_ERR_TIMEOUT : (int)(h[0] & 0xffffffff);
     if (blowup_step) *blowup_step = h[1];
     if (steps) *steps = c->steps;
     return LBM_OK;
@@ -573,6 +666,22 @@ int lbm_get_layout(const lbm_ctx* c, int* pitch, int* grid, int* block) {
     return LBM_OK;
 }
 
+int lbm_set_kernel_path(lbm_ctx* c, int path, int stages) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (path < LBM_PATH_AUTO || path > LBM_PATH_BULK || stages < 0 || stages == 1 || stages > 4)
+        return set_err(c, LBM_ERR_INVALID_ARG, "unknown kernel path or stage count");
+    if (path == LBM_PATH_BULK && !row_aligned(c))
+        return set_err(c, LBM_ERR_UNSUPPORTED, "the bulk-copy kernel needs rows of a multiple of 16 bytes");
+    c->path = path;
+    c->stages = stages;
+    if (c->own_group) {   // rebuilt with the new path at the next lbm_step
+        lbm_group_destroy(c->own_group);
+        c->own_group = nullptr;
+    }
+    c->gen += 1;
+    return LBM_OK;
+}
+
 int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_steps) {
     if (!out || !ctxs || n < 1 || graph_steps < 0 || (graph_steps % 2) != 0) return LBM_ERR_INVALID_ARG;
     *out = nullptr;
@@ -588,8 +697,46 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
     g->ctx.assign(ctxs, ctxs + n);
     g->stream = ctxs[0]->stream;
     g->graph_steps = graph_steps;
+    // lattices of one storage type whose rows are whole 16-byte chunks: one bulk-copy
+    // staged launch per time step (unless a context asks for the register-staged kernels)
+    bool tile = n <= lbm::kGroupMax;
+    for (int k = 0; tile && k < n; ++k)
+        tile = ctxs[k]->storage == ctxs[0]->storage && ctxs[k]->path != LBM_PATH_VECTOR && row_aligned(ctxs[k]);
+    if (tile) {
+        const int storage = ctxs[0]->storage;
+        const int stages = ctxs[0]->stages > 0 ? ctxs[0]->stages : default_stages(storage);
+        const int W = tile_width(storage);
+        unsigned off = 0;
+        for (int k = 0; k < n; ++k) {
+            g->tbegin.push_back(off);
+            off += tile_count(ctxs[k], W);
+        }
+        g->ttotal = off;
+        g->tsmem = tile_smem(storage, stages);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        for (int sh = 0; sh < 2 && tile; ++sh) {
+            const void* k = pick_tile_kernel(storage, sh == 1, stages);
+            int per_sm = 0;
+            if (!k || cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, g->tsmem) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, lbm::kTileThreads, g->tsmem) != cudaSuccess ||
+                per_sm < 1) {
+                cudaGetLastError();
+                tile = false;
+                break;
+            }
+            g->tkernel[sh] = k;
+            g->tgrid[sh] = (int)std::min<long long>((long long)sms * per_sm, (long long)off);
+        }
+        if (!tile) {
+            g->tbegin.clear();
+            g->ttotal = 0;
+        }
+        g->tiled = tile ? 1 : 0;
+    }
     // several lattices of one storage type: one fused launch per time step
-    bool same = n > 1 && n <= lbm::kGroupMax;
+    bool same = !g->tiled && n > 1 && n <= lbm::kGroupMax;
     for (int k = 1; same && k < n; ++k) same = ctxs[k]->storage == ctxs[0]->storage;
     if (same) {
         unsigned off = 0;
@@ -765,10 +912,16 @@ int lbm_adjoint_run(lbm_ctx* c, long long nsteps, int loss, const double* ux_tar
     cudaGraphExec_t seg_exec[2] = {nullptr, nullptr};
     cudaStream_t cap = nullptr;
     LBM_ADJ(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    // the recomputation takes the forward run's kernel family (the context's own group)
+    lbm_group* fg = (c->own_group && c->own_group->tiled) ? c->own_group : nullptr;
     auto enqueue_segment = [&](long long len, int parity, cudaStream_t st) {
         cudaError_t r = cudaSuccess;
-        for (long long k = 0; k + 1 < len && r == cudaSuccess; ++k)
-            r = lbm::adjoint_launch_fwd(plan, sa, ring + k * bufb, ring + (k + 1) * bufb, st);
+        for (long long k = 0; k + 1 < len && r == cudaSuccess; ++k) {
+            const void* a = ring + k * bufb;
+            void* b = ring + (k + 1) * bufb;
+            r = fg ? launch_tile(fg, &a, &b, st, is_shifted(c) ? 1 : 0)
+                   : lbm::adjoint_launch_fwd(plan, sa, a, b, st);
+        }
         int pl = parity;
         for (long long k = len - 1; k >= 0 && r == cudaSuccess; --k) {
             r = lbm::adjoint_launch_step(plan, ring + k * bufb, lam + pl * lamb, lam + (pl ^ 1) * lamb, rate_part, st);

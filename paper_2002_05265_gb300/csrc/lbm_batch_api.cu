@@ -249,6 +249,7 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_instance_desc* desc, int 
         I.a.rho0 = rho0;
         I.a.urx = d.ux_ref;
         I.a.ury = d.uy_ref;
+        lbm::fill_consts(I.a);
         I.model = d.model;
         I.pad = 0;
         I.ke_ref = d.ke_ref;

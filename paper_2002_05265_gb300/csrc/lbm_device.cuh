@@ -43,6 +43,11 @@ __host__ __device__ inline double shift_of(int i, double rho0, double urx, doubl
     return rho0 * phi1d(ex_of(i), urx) * phi1d(ey_of(i), ury);
 }
 
+// Collision constants, computed once on the host in both precisions (kernels then do no
+// FP64 set-up work, which GB300's narrow FP64 pipe would make costly):
+// [w_nu, w3, w4, rho0, urx, ury, Px0, Px+, Px-, Py0, Py+, Py-].
+constexpr int kNumConsts = 12;
+
 struct StepArgs {
     int nx, ny;          // lattice size
     int pitch;           // row pitch in elements
@@ -51,7 +56,20 @@ struct StepArgs {
     double w_nu, w3, w4; // relaxation frequencies of orders 2, 3, 4
     double rho0;         // shift reference density
     double urx, ury;     // shift reference velocity
+    double cd[kNumConsts];   // the constants above, FP64 (filled by fill_consts)
+    float cf[kNumConsts];    // the same, rounded to FP32
 };
+
+// Fills the constant tables of a StepArgs from its rates, rho0 and shift velocity.
+__host__ __device__ inline void fill_consts(StepArgs& a) {
+    const double v[kNumConsts] = {a.w_nu, a.w3, a.w4, a.rho0, a.urx, a.ury,
+                                  phi1d(0, a.urx), phi1d(1, a.urx), phi1d(-1, a.urx),
+                                  phi1d(0, a.ury), phi1d(1, a.ury), phi1d(-1, a.ury)};
+    for (int k = 0; k < kNumConsts; ++k) {
+        a.cd[k] = v[k];
+        a.cf[k] = (float)v[k];
+    }
+}
 
 // ---------------------------------------------------------------------------------------
 // Element conversions between the storage type S and the collision type T.
@@ -150,13 +168,17 @@ template <typename T> struct Consts {
     T w, w3, w4, rho0, urx, ury;
     T Px[3], Py[3];      // phi_s(u_ref) for s = 0, +1, -1 (shift factors)
 };
+template <typename T> __device__ __forceinline__ const T* const_table(const StepArgs& a);
+template <> __device__ __forceinline__ const float* const_table<float>(const StepArgs& a) { return a.cf; }
+template <> __device__ __forceinline__ const double* const_table<double>(const StepArgs& a) { return a.cd; }
+
 template <typename T>
 __device__ __forceinline__ Consts<T> make_consts(const StepArgs& a) {
+    const T* t = const_table<T>(a);
     Consts<T> c;
-    c.w = (T)a.w_nu; c.w3 = (T)a.w3; c.w4 = (T)a.w4; c.rho0 = (T)a.rho0;
-    c.urx = (T)a.urx; c.ury = (T)a.ury;
-    c.Px[0] = (T)phi1d(0, a.urx); c.Px[1] = (T)phi1d(1, a.urx); c.Px[2] = (T)phi1d(-1, a.urx);
-    c.Py[0] = (T)phi1d(0, a.ury); c.Py[1] = (T)phi1d(1, a.ury); c.Py[2] = (T)phi1d(-1, a.ury);
+    c.w = t[0]; c.w3 = t[1]; c.w4 = t[2]; c.rho0 = t[3]; c.urx = t[4]; c.ury = t[5];
+    c.Px[0] = t[6]; c.Px[1] = t[7]; c.Px[2] = t[8];
+    c.Py[0] = t[9]; c.Py[1] = t[10]; c.Py[2] = t[11];
     return c;
 }
 
@@ -475,10 +497,9 @@ struct GroupArgs {
 };
 
 template <typename S, bool SH>
-__device__ __forceinline__ void group_segment(const GroupEntry& e, unsigned local, int lane) {
-    using T = typename Conv<S>::T;
+__device__ __forceinline__ void group_segment(const GroupEntry& e, const Consts<typename Conv<S>::T>& c,
+                                              unsigned local, int lane) {
     constexpr int VEC = DefaultVec<S>::value;
-    const Consts<T> c = make_consts<T>(e.a);
     Diag dg;
     const unsigned s = local + lane;
     const S* src = static_cast<const S*>(e.src);
@@ -500,12 +521,13 @@ __device__ __forceinline__ void group_segment(const GroupEntry& e, unsigned loca
 
 template <typename S, bool SHIFT>
 __global__ void __launch_bounds__(256) group_step_kernel(const __grid_constant__ GroupArgs g) {
+    using T = typename Conv<S>::T;
     const int lane = threadIdx.x & 31;
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < g.padded_total; base += stride) {
         int k = 0;
         while (k + 1 < g.n && base >= g.e[k + 1].begin) ++k;
-        group_segment<S, SHIFT>(g.e[k], base - g.e[k].begin, lane);
+        group_segment<S, SHIFT>(g.e[k], make_consts<T>(g.e[k].a), base - g.e[k].begin, lane);
     }
 }
 

@@ -19,6 +19,13 @@ const void* group_kernel_f32(bool shifted);
 const void* group_kernel_f16(bool shifted);
 const void* group_kernel_bf16(bool shifted);
 
+// Bulk-copy staged step kernel (tile_step_kernel<S, shifted, stages>, one TileArgs parameter,
+// kTileThreads threads, tile_smem_bytes dynamic shared memory) per storage; stages 2-4.
+const void* tile_kernel_f64(bool shifted, int stages);
+const void* tile_kernel_f32(bool shifted, int stages);
+const void* tile_kernel_f16(bool shifted, int stages);
+const void* tile_kernel_bf16(bool shifted, int stages);
+
 // Batched persistent sweep kernel for (vector width, CTA size); nullptr if not instantiated.
 const void* batch_kernel_f64(int vec, int block);
 const void* batch_kernel_f32(int vec, int block);
@@ -64,6 +71,8 @@ struct AdjArgs {
     long long plane;
     double w_nu, w3, w4, rho0;
     double urx, ury;     // storage shift velocity
+    double cd[12];       // collision constants as in StepArgs (fill_consts), FP64 and FP32
+    float cf[12];
 };
 struct AdjointPlan {
     int storage;            // LBM_F64 or LBM_F32 (lambda kept in the collision precision)

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 LBM_BGK, LBM_RM, LBM_HM, LBM_CM, LBM_CHM, LBM_K, LBM_PR, LBM_RR = range(8)
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = range(4)
 LBM_PRESET_SRT, LBM_PRESET_REG = 0, 1
+LBM_PATH_AUTO, LBM_PATH_VECTOR, LBM_PATH_BULK = 0, 1, 2
 LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_CUDA, LBM_ERR_BLOWUP, LBM_ERR_TIMEOUT, LBM_ERR_NOMEM = \
     0, -1, -2, -3, -4, -5, -6
 
@@ -66,6 +67,7 @@ _SIGNATURES = {
     "lbm_status": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
     "lbm_synchronize": (_I, [_P]),
     "lbm_get_layout": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "lbm_set_kernel_path": (_I, [_P, _I, _I]),
     "lbm_group_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _I]),
     "lbm_group_step": (_I, [_P, _LL]),
     "lbm_group_destroy": (None, [_P]),
@@ -211,6 +213,10 @@ def lbm_get_layout(ctx):
     p, g, b = _I(), _I(), _I()
     _check(load_library().lbm_get_layout(ctx, ctypes.byref(p), ctypes.byref(g), ctypes.byref(b)), ctx)
     return p.value, g.value, b.value
+
+
+def lbm_set_kernel_path(ctx, path, stages=0):
+    _check(load_library().lbm_set_kernel_path(ctx, path, stages), ctx)
 
 
 def lbm_group_create(ctxs, graph_steps=64):
@@ -382,3 +388,6 @@ class Lattice:
 
     def set_shift_velocity(self, ux_ref, uy_ref):
         lbm_set_shift_velocity(self.ctx, ux_ref, uy_ref)
+
+    def set_kernel_path(self, path, stages=0):
+        lbm_set_kernel_path(self.ctx, path, stages)

@@ -1,0 +1,185 @@
+"""The two step-kernel families on lattices with several tiles per row and a short last tile:
+the copy-engine staged kernel (LBM_PATH_BULK, cp.async.bulk into a ring of 2-4 shared-memory
+stages) and the register-staged kernels (LBM_PATH_VECTOR), each against the FP64 oracle and
+against each other.  Tile widths: 512 (FP64), 1024 (FP32), 2048 (FP16, BF16) nodes."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2002_05265_gb300 import flows  # noqa: E402
+import oracle.lbm as olbm  # noqa: E402
+from oracle.collision import macroscopic  # noqa: E402
+
+MODELS = ["bgk", "rm", "hm", "cm", "chm", "k", "pr", "rr"]
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_05265_gb300 import build, lbm
+    build.build_library()
+    lbm.load_library()
+    return lbm
+
+
+def _dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+def _run(L, fields, model, rates, storage, steps, path, stages=0, shift=None):
+    rho, ux, uy = fields
+    ny, nx = rho.shape
+    lat = L.Lattice(nx, ny, L.MODELS[model], rates, storage=storage)
+    lat.set_kernel_path(path, stages)
+    if shift is not None:
+        lat.set_shift_velocity(*shift)
+    lat.init_equilibrium(*_dev(rho, ux, uy))
+    lat.step(steps)
+    st = lat.status()
+    f = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+    lat.get_populations(f)
+    lat.close()
+    assert st[0] == L.LBM_OK
+    return f.cpu().numpy()
+
+
+def _vel_err(got, ref):
+    _, gx, gy = macroscopic(got)
+    _, rx, ry = macroscopic(ref)
+    return max(np.max(np.abs(gx - rx)), np.max(np.abs(gy - ry)))
+
+
+def _l2(got, ref):
+    _, gx, gy = macroscopic(got)
+    _, rx, ry = macroscopic(ref)
+    return float(np.sqrt(((gx - rx) ** 2 + (gy - ry) ** 2).sum() / (rx ** 2 + ry ** 2).sum()))
+
+
+@pytest.mark.parametrize("stages", [2, 3, 4])
+@pytest.mark.parametrize("model", MODELS)
+def test_bulk_fp64_three_tiles_per_row(L, model, stages):
+    """FP64, 1030 x 6 (tiles of 512, 512 and 6 nodes; periodic wrap in x and y at every
+    tile edge), Ma = 0.3 vortex with noise, 40 steps: within 1e-12 of the oracle."""
+    fields = flows.vortex(1030, 6, Ma=0.3, radius_frac=0.004, noise=1e-6, seed=21)
+    rates = olbm.rates_from_nu(1e-3, "reg" if model in ("chm", "k") else "srt")
+    got = _run(L, fields, model, rates, L.LBM_F64, 40, L.LBM_PATH_BULK, stages)
+    ref = olbm.run(olbm.init_equilibrium(*fields), model, rates, 40)
+    assert float(np.max(np.abs(got - ref) / np.abs(ref))) <= 1e-12
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_bulk_and_vector_fp32_agree_with_oracle(L, model):
+    """FP32, 2060 x 5 (tiles of 1024, 1024 and 12 nodes), 200 steps: both kernel families
+    within 1e-5 of the oracle's velocity, and within 1e-6 of each other's populations."""
+    fields = flows.vortex(2060, 5, Ma=0.2, radius_frac=0.002, noise=1e-6, seed=22)
+    rates = olbm.rates_from_nu(1e-4, "reg" if model in ("chm", "k") else "srt")
+    bulk = _run(L, fields, model, rates, L.LBM_F32, 200, L.LBM_PATH_BULK)
+    vec = _run(L, fields, model, rates, L.LBM_F32, 200, L.LBM_PATH_VECTOR)
+    ref = olbm.run(olbm.init_equilibrium(*fields), model, rates, 200)
+    assert _vel_err(bulk, ref) <= 1e-5
+    assert _vel_err(vec, ref) <= 1e-5
+    assert float(np.max(np.abs(bulk - vec))) <= 1e-6
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("model", ["bgk", "cm", "k", "rr"])
+def test_bulk_16bit_two_tiles_per_row(L, model, storage):
+    """FP16 / BF16, 2072 x 4 (tiles of 2048 and 24 nodes), 300 steps, with and without a
+    reference-velocity shift: the bulk-copy kernel's velocity error against the oracle stays
+    within the bound of the register-staged kernel (same arithmetic, same roundings)."""
+    st = L.LBM_F16 if storage == "f16" else L.LBM_BF16
+    bound = 5e-3 if storage == "f16" else 4e-2
+    fields = flows.vortex(2072, 4, Ma=0.1, radius_frac=0.002, noise=1e-8, seed=23)
+    rates = olbm.rates_from_nu(1e-4, "reg" if model in ("cm", "k") else "srt")
+    ref = olbm.run(olbm.init_equilibrium(*fields), model, rates, 300)
+    for shift in (None, (0.1 / np.sqrt(3.0), 0.0)):
+        bulk = _run(L, fields, model, rates, st, 300, L.LBM_PATH_BULK, shift=shift)
+        vec = _run(L, fields, model, rates, st, 300, L.LBM_PATH_VECTOR, shift=shift)
+        assert _l2(bulk, ref) <= bound
+        assert _l2(vec, ref) <= bound
+        assert _l2(bulk, vec) <= bound
+
+
+def test_bulk_multi_lattice_group(L):
+    """Three FP32 lattices of different sizes and models (1 to 3 tiles per row) advanced by
+    one bulk-copy launch per step equal the same lattices stepped one by one."""
+    shapes = [(2060, 7, "chm"), (1024, 9, "k"), (96, 40, "bgk")]
+    rates = olbm.rates_from_nu(1e-4, "reg")
+    lats, refs = [], []
+    for nx, ny, m in shapes:
+        fields = flows.vortex(nx, ny, Ma=0.2, radius_frac=0.01, noise=1e-6, seed=nx + ny)
+        for group in (lats, refs):
+            lat = L.Lattice(nx, ny, L.MODELS[m], rates, storage=L.LBM_F32)
+            lat.set_kernel_path(L.LBM_PATH_BULK)
+            lat.init_equilibrium(*_dev(*fields))
+            group.append(lat)
+    g = L.lbm_group_create([x.ctx for x in lats], graph_steps=8)
+    L.lbm_group_step(g, 37)
+    for r in refs:
+        r.step(37)
+    for (nx, ny, _), x, r in zip(shapes, lats, refs):
+        fa = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+        fb = torch.empty_like(fa)
+        x.get_populations(fa)
+        r.get_populations(fb)
+        assert torch.equal(fa, fb)
+        assert x.status()[0] == L.LBM_OK
+    L.lbm_group_destroy(g)
+    for lat in lats + refs:
+        lat.close()
+
+
+def test_kernel_path_argument_checks(L):
+    lat = L.Lattice(99, 10, L.LBM_BGK, (1.5, 1.5, 1.5), storage=L.LBM_F32)
+    with pytest.raises(L.LBMError) as e:
+        lat.set_kernel_path(L.LBM_PATH_BULK)          # 99 * 4 bytes is not a multiple of 16
+    assert e.value.code == L.LBM_ERR_UNSUPPORTED
+    for path, stages in ((3, 0), (-1, 0), (L.LBM_PATH_AUTO, 1), (L.LBM_PATH_AUTO, 5)):
+        with pytest.raises(L.LBMError) as e:
+            lat.set_kernel_path(path, stages)
+        assert e.value.code == L.LBM_ERR_INVALID_ARG
+    lat.set_kernel_path(L.LBM_PATH_AUTO)              # falls back to the register-staged kernels
+    lat.close()
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("shape", [(70, 9), (64, 37), (96, 17)])
+def test_bulk_fp64_row_block_tiles(L, model, shape):
+    """FP64 lattices narrower than half a tile move as blocks of whole rows: 70 x 9 (pitch 96
+    != nx: one copy per row; blocks of 7 and 2 rows), 64 x 37 (pitch == nx: consecutive rows
+    in one copy, split at the periodic wrap; 8 rows per block, last block 5), 96 x 17.  Within
+    1e-12 of the oracle after 30 steps."""
+    nx, ny = shape
+    fields = flows.vortex(nx, ny, Ma=0.3, radius_frac=0.1, noise=1e-6, seed=nx * ny)
+    rates = olbm.rates_from_nu(1e-3, "reg" if model in ("chm", "k") else "srt")
+    got = _run(L, fields, model, rates, L.LBM_F64, 30, L.LBM_PATH_BULK, 3)
+    ref = olbm.run(olbm.init_equilibrium(*fields), model, rates, 30)
+    assert float(np.max(np.abs(got - ref) / np.abs(ref))) <= 1e-12
+
+
+@pytest.mark.parametrize("storage,shape", [("f32", (100, 23)), ("f32", (64, 37)), ("f16", (136, 17)),
+                                           ("bf16", (64, 70))])
+def test_bulk_row_block_tiles_reduced_precision(L, storage, shape):
+    """Row-block tiles in FP32 (blocks of 10 rows with pitch 128 != nx = 100; blocks of 16
+    dense rows) and 16-bit storage: the bulk-copy kernel agrees with the register-staged
+    kernel (FP32: 1e-6 on populations) and with the oracle (FP32 1e-5 on u; FP16 / BF16 the
+    storage bounds) after 200 steps, for the CHM model."""
+    nx, ny = shape
+    st = {"f32": L.LBM_F32, "f16": L.LBM_F16, "bf16": L.LBM_BF16}[storage]
+    fields = flows.vortex(nx, ny, Ma=0.1, radius_frac=0.1, noise=1e-8, seed=nx + 7 * ny)
+    rates = olbm.rates_from_nu(1e-4, "reg")
+    bulk = _run(L, fields, "chm", rates, st, 200, L.LBM_PATH_BULK)
+    vec = _run(L, fields, "chm", rates, st, 200, L.LBM_PATH_VECTOR)
+    ref = olbm.run(olbm.init_equilibrium(*fields), "chm", rates, 200)
+    if storage == "f32":
+        assert _vel_err(bulk, ref) <= 1e-5
+        assert float(np.max(np.abs(bulk - vec))) <= 1e-6
+    else:
+        bound = 5e-3 if storage == "f16" else 4e-2
+        assert _l2(bulk, ref) <= bound
+        assert _l2(bulk, vec) <= bound
