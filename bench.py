@@ -66,10 +66,21 @@ def parse():
                    help="step-kernel family: copy-engine staged (bulk), register-staged (vector), or the "
                         "library's choice (auto: bulk where the row length allows it)")
     p.add_argument("--stages", type=int, default=0, help="shared-memory stages of the bulk-copy kernel (0 = default)")
+    p.add_argument("--launch-steps", type=int, default=0,
+                   help="time steps per bulk-copy launch (0 = the library's default)")
+    p.add_argument("--order", default="auto", choices=["auto", "step", "wave"],
+                   help="work order of multi-step bulk-copy launches (auto: wavefront when the state exceeds 64 MB)")
     return p.parse_args()
 
 
 PATHS = {"auto": 0, "vector": 1, "bulk": 2}
+ORDERS = {"auto": 0, "step": 1, "wave": 2}
+
+
+def shape_lattice(lat, args):
+    """Kernel family and launch shape of a benchmark lattice from the command line."""
+    lat.set_kernel_path(PATHS[args.path], args.stages)
+    lat.set_launch_shape(args.launch_steps, ORDERS[args.order])
 
 
 def dist_setup(args):
@@ -206,7 +217,7 @@ def cpu_baseline(n_models=len(MODELS)):
                       f"({lu} lattice updates, {dt:.1f} s), numpy FP64 single-threaded"}
 
 
-def adjoint_ratio(lbm, flows, stream):
+def adjoint_ratio(lbm, flows, stream, path=0, stages=0):
     """Adjoint / forward time ratio on the 512 x 512 vortex, 4000 steps, FP32, REG rates,
     misfit loss, sqrt(N) checkpoints: backward (recomputation + adjoint steps) over the plain
     forward run of the same 4000 steps."""
@@ -220,6 +231,7 @@ def adjoint_ratio(lbm, flows, stream):
     res = {}
     for m in ("chm", "k"):
         lat = lbm.Lattice(N, N, lbm.MODELS[m], (w, 1.0, 1.0), storage=lbm.LBM_F32, stream=stream)
+        lat.set_kernel_path(path, stages)
         lat.init_equilibrium(*dev[:3])
         lat.step(64)
         lat.synchronize()
@@ -337,15 +349,17 @@ def run_sweep(args):
         for m in models:
             rates = lbm.lbm_rates_from_nu(1e-6, lbm.LBM_PRESET_SRT if _preset(m) == "srt" else lbm.LBM_PRESET_REG)
             lat = lbm.Lattice(n, n, lbm.MODELS[m], rates, storage=lbm.STORAGES[s], stream=stream)
-            lat.set_kernel_path(PATHS[args.path], args.stages)
+            shape_lattice(lat, args)
             lat.init_equilibrium(*fields)
-            g = lbm.lbm_group_create([lat.ctx], graph_steps=2)
-            lbm.lbm_group_step(g, max(2, args.warmup - args.warmup % 2), lat.ctx)
+            # graphs of 16 steps (room for multi-step launches); counts rounded to whole graphs
+            g = lbm.lbm_group_create([lat.ctx], graph_steps=16)
+            lbm.lbm_group_step(g, 16 * max(1, -(-args.warmup // 16)), lat.ctx)
             lbm.lbm_group_set_timing(g, True)
-            lbm.lbm_group_step(g, args.steps - args.steps % 2, lat.ctx)
+            lbm.lbm_group_step(g, 16 * max(1, args.steps // 16), lat.ctx)
             rms, nl, _ = lbm.lbm_group_timing(g)
             t = rms / 1e3 / nl
             print(json.dumps({"sweep": True, "model": m, "storage": s, "path": args.path, "stages": args.stages,
+                              "launch_steps": args.launch_steps, "order": args.order,
                               "lattice": f"{n}x{n}", "steps": nl,
                               "glups": n * n / t / 1e9, "gbs": BYTES_PER_LU[s] * n * n / t / 1e9,
                               "ms_per_step": t * 1e3}), flush=True)
@@ -477,7 +491,7 @@ def main():
     for m in MODELS:
         rates = lbm.lbm_rates_from_nu(NU, lbm.LBM_PRESET_SRT if _preset(m) == "srt" else lbm.LBM_PRESET_REG)
         lat = lbm.Lattice(L, L, lbm.MODELS[m], rates, storage=lbm.LBM_F32, stream=stream)
-        lat.set_kernel_path(PATHS[args.path], args.stages)
+        shape_lattice(lat, args)
         lat.set_check(CHECK_EVERY)
         lats.append(lat)
     group = lbm.lbm_group_create([x.ctx for x in lats], graph_steps=GRAPH_STEPS)
@@ -535,9 +549,13 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind, "launch_us": avg_launch_s * 1e6,
                 "bytes_per_launch": bytes_per_launch,
-                "kernel": kname + ": one launch = one time step of the 8 lattices, 72 B per lattice update"}
+                "kernel": kname + f": one launch = {lattice_steps // kernel_launches // len(MODELS)} time step(s) "
+                          "of the 8 lattices, 72 B per lattice update"}
 
-    launches_per_step = S + len(MODELS) * (1 + 2 * (S // CHECK_EVERY) + 1)
+    # step-kernel launches counted by the group's replay timing (one multi-step launch per
+    # replay for the bulk-copy kernel, one per time step otherwise), plus per lattice: the
+    # equilibrium init, two reduction kernels per check, the moments gather
+    launches_per_step = kernel_launches // args.steps + len(MODELS) * (1 + 2 * (S // CHECK_EVERY) + 1)
 
     e2e = None
     if not args.no_e2e:
@@ -561,7 +579,7 @@ def main():
         for m in MODELS:
             rates = lbm.lbm_rates_from_nu(NU, lbm.LBM_PRESET_SRT if _preset(m) == "srt" else lbm.LBM_PRESET_REG)
             big = lbm.Lattice(4096, 4096, lbm.MODELS[m], rates, storage=lbm.LBM_F32, stream=stream)
-            big.set_kernel_path(PATHS[args.path], args.stages)
+            shape_lattice(big, args)
             f4 = flows.double_shear_layer(4096, Ma=MA)
             big.init_equilibrium(*[torch.from_numpy(a).cuda() for a in f4])
             g1 = lbm.lbm_group_create([big.ctx], graph_steps=32)
@@ -577,7 +595,7 @@ def main():
 
     adjoint = None
     if not args.no_adjoint:
-        adjoint = adjoint_ratio(lbm, flows, stream)
+        adjoint = adjoint_ratio(lbm, flows, stream, PATHS[args.path], args.stages)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -202,6 +202,25 @@ int lbm_get_layout(const lbm_ctx* ctx, int* pitch, int* grid, int* block);
 enum { LBM_PATH_AUTO = 0, LBM_PATH_VECTOR = 1, LBM_PATH_BULK = 2 };
 int lbm_set_kernel_path(lbm_ctx* ctx, int path, int stages);
 
+/* Launch shape of the copy-engine staged kernel (library design choice; the paper has no
+ * counterpart; results are identical for every shape).  One launch may advance several time
+ * steps: a tile of step s is copied once the rows it pulls from are complete in step s - 1
+ * (row-completion counters in device memory, cooperative launch).
+ *   steps_per_launch  time steps per launch; 0 = default (16 with the wavefront order, many
+ *                     for lattices with few tiles per CTA, else 1).
+ *   order             LBM_ORDER_STEP: every tile of step s before those of step s + 1 (in
+ *                     the CTAs' round-robin).  LBM_ORDER_WAVE (lattices of one geometry):
+ *                     the steps of a launch interleave, a few rows behind one another, so
+ *                     the intermediate states stay in the L2 and HBM sees about one read and
+ *                     two writes per launch instead of one read and one write per step.
+ *                     LBM_ORDER_AUTO: the wavefront when both buffers of the lattices exceed
+ *                     64 MB, else step order.
+ * Applies to the context's next lbm_step and to groups created afterwards (a group takes the
+ * shape of its first context).  Errors: LBM_ERR_INVALID_ARG for a negative step count or an
+ * unknown order. */
+enum { LBM_ORDER_AUTO = 0, LBM_ORDER_STEP = 1, LBM_ORDER_WAVE = 2 };
+int lbm_set_launch_shape(lbm_ctx* ctx, int steps_per_launch, int order);
+
 /* Several contexts advanced together, one time step of each in turn (so a set of lattices
  * whose sum exceeds L2 streams from HBM as a single large one would), captured in CUDA
  * graphs of `graph_steps` steps (even, >= 2; 0 = no graphs).  Every context must use the

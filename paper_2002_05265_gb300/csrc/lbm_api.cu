@@ -43,6 +43,8 @@ struct lbm_ctx {
     double ke_ref = 0.0, ke_factor = 1.0, uref_x = 0.0, uref_y = 0.0;
     int path = LBM_PATH_AUTO;          // kernel family (lbm_set_kernel_path)
     int stages = 0;                    // bulk-copy ring stages, 0 = default
+    int launch_steps = 0;              // bulk-copy time steps per launch, 0 = default (lbm_set_launch_shape)
+    int launch_order = LBM_ORDER_AUTO; // bulk-copy work order
     lbm_group* own_group = nullptr;    // used by lbm_step
     unsigned gen = 0;                  // bumped when kernel arguments change (graphs re-record)
     char err[512] = {0};
@@ -61,6 +63,12 @@ struct lbm_group {
     int tsmem = 0;                     // dynamic shared memory of the bulk-copy kernel
     std::vector<unsigned> tbegin;      // first tile of each context
     unsigned ttotal = 0;
+    std::vector<unsigned> cbase;       // first completion counter of each context
+    unsigned* cnt = nullptr;           // completion counters of multi-step launches (device)
+    unsigned cunits = 0;
+    int same_geometry = 0;             // every context has the same units and tiles per unit
+    int wU = 0, wntx = 0;              // that geometry
+    long long state_bytes = 0;         // both buffers of every context
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;
     int graph_steps = 0;
@@ -263,19 +271,26 @@ int launch_group_once(lbm_group* g, cudaStream_t s, int sh) {
     return LBM_OK;
 }
 
-// bulk-copy staged launch of a tiled group: one time step of every context, from src[k] to
-// dst[k] (the contexts' own buffers, or the recomputation ring of the adjoint)
-cudaError_t launch_tile(lbm_group* g, const void* const* src, void* const* dst, cudaStream_t s, int sh) {
+// bulk-copy staged launch of a tiled group: `nsteps` time steps of every context k, reading
+// buf0[k] at the first step (buffers buf0[k] and buf1[k] alternate; with nsteps = 1 they are
+// simply source and destination, as for the recomputation ring of the adjoint)
+cudaError_t launch_tile(lbm_group* g, const void* const* buf0, void* const* buf1, int nsteps, cudaStream_t s,
+                        int sh, long long ring = 0) {
     lbm::TileArgs ta;
     ta.n = (int)g->ctx.size();
     ta.total = g->ttotal;
+    ta.nsteps = nsteps;
     ta.flag = g->ctx[0]->status + 1;   // second int of the first context's status word
+    ta.cnt = g->cnt;
     const int W = tile_width(g->ctx[0]->storage);
     for (size_t k = 0; k < g->ctx.size(); ++k) {
         lbm_ctx* c = g->ctx[k];
         lbm::TileEntry& e = ta.e[k];
-        e.src = src[k];
-        e.dst = dst[k];
+        e.buf[0] = buf0[k];
+        e.buf[1] = buf1[k];
+        e.cur = 0;
+        e.ring = ring;
+        e.cbase = g->cbase[k];
         e.a = step_args(c);
         e.model = c->model;
         e.eq_order = c->eq_order;
@@ -283,33 +298,76 @@ cudaError_t launch_tile(lbm_group* g, const void* const* src, void* const* dst, 
         e.ntx = e.rows > 1 ? 0 : (c->nx + W - 1) / W;
         e.begin = g->tbegin[k];
     }
+    // work order: wavefront for multi-step launches of one geometry when asked, or by default
+    // when the state does not fit in about half the L2 (then the interleaved steps reuse it)
+    ta.wave = 0;
+    ta.wU = ta.wntx = ta.wD = 0;
+    ta.witems = 0;
+    const int order = g->ctx[0]->launch_order;
+    unsigned long long items = (unsigned long long)nsteps * g->ttotal;
+    if (nsteps > 1 && g->same_geometry && order != LBM_ORDER_STEP &&
+        (order == LBM_ORDER_WAVE || g->state_bytes > (64ll << 20))) {
+        // skew: a dependency lies about two grid-widths of work items back
+        const long long per_key = (long long)nsteps * (long long)ta.n * g->wntx;
+        const int D = (int)std::max<long long>(4, (2LL * g->tgrid[sh] + per_key - 1) / per_key + 1);
+        const unsigned long long w = (unsigned long long)(g->wU + (long long)(nsteps - 1) * D) * per_key;
+        if (w < (1ull << 32)) {
+            ta.wave = 1;
+            ta.wU = g->wU;
+            ta.wntx = g->wntx;
+            ta.wD = D;
+            ta.witems = (unsigned)w;
+            items = w;
+        }
+    }
+    if (items >= (1ull << 32)) return cudaErrorInvalidValue;   // the caller splits longer runs
+    cudaError_t e = cudaSuccess;
+    if (nsteps > 1) e = cudaMemsetAsync(g->cnt, 0, sizeof(unsigned) * g->cunits, s);
+    if (e != cudaSuccess) return e;
+    int grid = (int)std::min<unsigned long long>((unsigned long long)g->tgrid[sh], items);
+    // wavefront items cycle fastest through segments, lattices and steps (power-of-two
+    // extents in practice); an odd grid keeps a CTA from being pinned to one lattice or step
+    if (ta.wave && grid > 1 && (grid % 2) == 0) grid -= 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(lbm::kTileThreads);
+    cfg.dynamicSmemBytes = (size_t)g->tsmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // CTAs of a multi-step launch wait on one another
+    attr[0].val.cooperative = nsteps > 1 ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     void* args[] = {(void*)&ta};
-    return cudaLaunchKernel(g->tkernel[sh], dim3(g->tgrid[sh]), dim3(lbm::kTileThreads), args, (size_t)g->tsmem, s);
+    return cudaLaunchKernelExC(&cfg, g->tkernel[sh], args);
 }
 
-// one time step of every context of a tiled group, as one bulk-copy staged launch
-int launch_tile_once(lbm_group* g, cudaStream_t s, int sh) {
-    std::vector<const void*> src(g->ctx.size());
-    std::vector<void*> dst(g->ctx.size());
+// `n` time steps of every context of a tiled group in one bulk-copy staged launch
+int launch_tile_steps(lbm_group* g, cudaStream_t s, int sh, int n) {
+    std::vector<const void*> b0(g->ctx.size());
+    std::vector<void*> b1(g->ctx.size());
     for (size_t k = 0; k < g->ctx.size(); ++k) {
-        src[k] = g->ctx[k]->buf[g->ctx[k]->cur];
-        dst[k] = g->ctx[k]->buf[g->ctx[k]->cur ^ 1];
+        b0[k] = g->ctx[k]->buf[g->ctx[k]->cur];
+        b1[k] = g->ctx[k]->buf[g->ctx[k]->cur ^ 1];
     }
-    LBM_CK(g->ctx[0], launch_tile(g, src.data(), dst.data(), s, sh));
+    LBM_CK(g->ctx[0], launch_tile(g, b0.data(), b1.data(), n, s, sh));
     for (lbm_ctx* c : g->ctx) {
-        c->cur ^= 1;
-        c->steps += 1;
+        c->cur ^= (n & 1);
+        c->steps += n;
     }
     return LBM_OK;
 }
 
+// shift family of a tiled group's launch: 0 / 1 when every context uses the default /
+// reference-velocity shift, -1 when they differ (then each context is stepped on its own)
+int tile_shift(const lbm_group* g) {
+    int nsh = 0;
+    for (lbm_ctx* c : g->ctx) nsh += is_shifted(c) ? 1 : 0;
+    return nsh == 0 ? 0 : (nsh == (int)g->ctx.size() ? 1 : -1);
+}
+
 int group_step_once(lbm_group* g, cudaStream_t s) {
-    if (g->tiled) {
-        int nsh = 0;
-        for (lbm_ctx* c : g->ctx) nsh += is_shifted(c) ? 1 : 0;
-        if (nsh == 0) return launch_tile_once(g, s, 0);
-        if (nsh == (int)g->ctx.size()) return launch_tile_once(g, s, 1);
-    }
+    if (g->tiled && tile_shift(g) >= 0) return launch_tile_steps(g, s, tile_shift(g), 1);
     if (g->fused) {
         int nsh = 0;
         for (lbm_ctx* c : g->ctx) nsh += is_shifted(c) ? 1 : 0;
@@ -318,6 +376,51 @@ int group_step_once(lbm_group* g, cudaStream_t s) {
     }
     for (lbm_ctx* c : g->ctx) {
         int rc = launch_step_once(c, s);
+        if (rc != LBM_OK) return rc;
+    }
+    return LBM_OK;
+}
+
+// Most time steps in one launch of the bulk-copy kernel (longer runs are split).
+#ifndef LBM_TILE_STEPS_PER_LAUNCH
+#define LBM_TILE_STEPS_PER_LAUNCH (1 << 20)
+#endif
+
+// Steps per launch of a tiled group: a launch whose step has few tiles per CTA loses a
+// noticeable share of its time to ramping up and draining the copy pipeline, so such groups
+// run many steps per launch (with the row-completion counters); large lattices run one step
+// per launch, where the counters' fences would only add latency to the copy pipeline.
+int tile_steps_per_launch(const lbm_group* g) {
+    int per;
+    if (g->ctx[0]->launch_steps > 0) {
+        per = g->ctx[0]->launch_steps;
+    } else if (g->same_geometry && g->ctx[0]->launch_order != LBM_ORDER_STEP &&
+               (g->ctx[0]->launch_order == LBM_ORDER_WAVE || g->state_bytes > (64ll << 20))) {
+        per = 16;   // wavefront: the intermediate states stay in the L2
+    } else {
+        const int grid = std::max(1, std::max(g->tgrid[0], g->tgrid[1]));
+        per = g->ttotal < 64u * (unsigned)grid ? LBM_TILE_STEPS_PER_LAUNCH : 1;
+    }
+    // keep the work items of one launch within 32 bits
+    const long long cap = std::max<long long>(1, ((1ll << 31) / std::max(1u, g->ttotal)) / 2);
+    return (int)std::min<long long>(std::min<long long>(per, cap), LBM_TILE_STEPS_PER_LAUNCH);
+}
+
+// n time steps of the group: bulk-copy launches for a tiled group, else n launches
+int group_advance(lbm_group* g, cudaStream_t s, long long n) {
+    if (n <= 0) return LBM_OK;
+    if (g->tiled && tile_shift(g) >= 0) {
+        const int per = tile_steps_per_launch(g);
+        for (long long done = 0; done < n;) {
+            const int chunk = (int)std::min<long long>(n - done, per);
+            int rc = launch_tile_steps(g, s, tile_shift(g), chunk);
+            if (rc != LBM_OK) return rc;
+            done += chunk;
+        }
+        return LBM_OK;
+    }
+    for (long long t = 0; t < n; ++t) {
+        int rc = group_step_once(g, s);
         if (rc != LBM_OK) return rc;
     }
     return LBM_OK;
@@ -346,7 +449,7 @@ int group_record(lbm_group* g) {
     for (size_t k = 0; k < g->ctx.size(); ++k) { cur0[k] = g->ctx[k]->cur; steps0[k] = g->ctx[k]->steps; }
     LBM_CK(c0, cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
     int rc = LBM_OK;
-    for (int t = 0; t < g->graph_steps && rc == LBM_OK; ++t) rc = group_step_once(g, g->capture);
+    rc = group_advance(g, g->capture, g->graph_steps);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(g->capture, &graph);
     for (size_t k = 0; k < g->ctx.size(); ++k) { g->ctx[k]->cur = cur0[k]; g->ctx[k]->steps = steps0[k]; }
@@ -394,7 +497,9 @@ int group_replay(lbm_group* g) {
     if (g->timing) {
         LBM_CK(c0, cudaEventRecord(e1, g->stream));
         g->pending_lattice_steps += (long long)g->graph_steps * (long long)g->ctx.size();
-        g->pending_kernels += (long long)g->graph_steps * ((g->fused || g->tiled) ? 1LL : (long long)g->ctx.size());
+        g->pending_kernels += (g->tiled && tile_shift(g) >= 0)
+                                  ? (long long)(g->graph_steps + tile_steps_per_launch(g) - 1) / tile_steps_per_launch(g)
+                                  : (long long)g->graph_steps * (g->fused ? 1LL : (long long)g->ctx.size());
     }
     for (lbm_ctx* c : g->ctx) c->steps += g->graph_steps;   // even: buffers end where they began
     return LBM_OK;
@@ -682,6 +787,20 @@ int lbm_set_kernel_path(lbm_ctx* c, int path, int stages) {
     return LBM_OK;
 }
 
+int lbm_set_launch_shape(lbm_ctx* c, int steps_per_launch, int order) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (steps_per_launch < 0 || order < LBM_ORDER_AUTO || order > LBM_ORDER_WAVE)
+        return set_err(c, LBM_ERR_INVALID_ARG, "invalid steps per launch or work order");
+    c->launch_steps = steps_per_launch;
+    c->launch_order = order;
+    if (c->own_group) {   // rebuilt at the next lbm_step
+        lbm_group_destroy(c->own_group);
+        c->own_group = nullptr;
+    }
+    c->gen += 1;
+    return LBM_OK;
+}
+
 int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_steps) {
     if (!out || !ctxs || n < 1 || graph_steps < 0 || (graph_steps % 2) != 0) return LBM_ERR_INVALID_ARG;
     *out = nullptr;
@@ -707,9 +826,29 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
         const int stages = ctxs[0]->stages > 0 ? ctxs[0]->stages : default_stages(storage);
         const int W = tile_width(storage);
         unsigned off = 0;
+        unsigned units = 0;
+        g->same_geometry = 1;
         for (int k = 0; k < n; ++k) {
             g->tbegin.push_back(off);
             off += tile_count(ctxs[k], W);
+            g->cbase.push_back(units);
+            const int R = tile_rows(ctxs[k], W);
+            const int U = R > 1 ? (ctxs[k]->ny + R - 1) / R : ctxs[k]->ny;
+            const int ntx = R > 1 ? 1 : (ctxs[k]->nx + W - 1) / W;
+            units += (unsigned)U;
+            if (k == 0) {
+                g->wU = U;
+                g->wntx = ntx;
+            } else if (U != g->wU || ntx != g->wntx || R != tile_rows(ctxs[0], W)) {
+                g->same_geometry = 0;
+            }
+            g->state_bytes += 2LL * 9 * ctxs[k]->plane * lbm::storage_bytes(storage);
+        }
+        g->cunits = units;
+        if (cudaMalloc(&g->cnt, sizeof(unsigned) * units) != cudaSuccess) {
+            cudaGetLastError();
+            g->cnt = nullptr;
+            tile = false;
         }
         g->ttotal = off;
         g->tsmem = tile_smem(storage, stages);
@@ -727,11 +866,14 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
                 break;
             }
             g->tkernel[sh] = k;
-            g->tgrid[sh] = (int)std::min<long long>((long long)sms * per_sm, (long long)off);
+            g->tgrid[sh] = sms * per_sm;   // all resident CTAs (a multi-step launch needs them co-resident)
         }
         if (!tile) {
             g->tbegin.clear();
+            g->cbase.clear();
             g->ttotal = 0;
+            if (g->cnt) cudaFree(g->cnt);
+            g->cnt = nullptr;
         }
         g->tiled = tile ? 1 : 0;
     }
@@ -769,6 +911,7 @@ void lbm_group_destroy(lbm_group* g) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     if (g->capture) cudaStreamDestroy(g->capture);
+    if (g->cnt) cudaFree(g->cnt);
     delete g;
 }
 
@@ -789,10 +932,8 @@ int lbm_group_step(lbm_group* g, long long nsteps) {
             if (rc) return rc;
             left -= g->graph_steps;
         }
-        for (long long t = 0; t < left; ++t) {
-            int rc = group_step_once(g, g->stream);
-            if (rc) return rc;
-        }
+        int rc = group_advance(g, g->stream, left);
+        if (rc) return rc;
         done += chunk;
         for (lbm_ctx* c : g->ctx)
             if (c->check_every > 0 && c->steps % c->check_every == 0) {
@@ -916,12 +1057,14 @@ int lbm_adjoint_run(lbm_ctx* c, long long nsteps, int loss, const double* ux_tar
     lbm_group* fg = (c->own_group && c->own_group->tiled) ? c->own_group : nullptr;
     auto enqueue_segment = [&](long long len, int parity, cudaStream_t st) {
         cudaError_t r = cudaSuccess;
-        for (long long k = 0; k + 1 < len && r == cudaSuccess; ++k) {
-            const void* a = ring + k * bufb;
-            void* b = ring + (k + 1) * bufb;
-            r = fg ? launch_tile(fg, &a, &b, st, is_shifted(c) ? 1 : 0)
-                   : lbm::adjoint_launch_fwd(plan, sa, a, b, st);
+        if (fg && len > 1) {   // the whole recomputation in one multi-step launch along the ring
+            const void* a = ring;
+            void* b = ring;
+            r = launch_tile(fg, &a, &b, (int)(len - 1), st, is_shifted(c) ? 1 : 0,
+                            (long long)(bufb / lbm::storage_bytes(c->storage)));
         }
+        for (long long k = 0; !fg && k + 1 < len && r == cudaSuccess; ++k)
+            r = lbm::adjoint_launch_fwd(plan, sa, ring + k * bufb, ring + (k + 1) * bufb, st);
         int pl = parity;
         for (long long k = len - 1; k >= 0 && r == cudaSuccess; --k) {
             r = lbm::adjoint_launch_step(plan, ring + k * bufb, lam + pl * lamb, lam + (pl ^ 1) * lamb, rate_part, st);

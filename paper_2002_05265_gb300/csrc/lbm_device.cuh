@@ -45,8 +45,8 @@ __host__ __device__ inline double shift_of(int i, double rho0, double urx, doubl
 
 // Collision constants, computed once on the host in both precisions (kernels then do no
 // FP64 set-up work, which GB300's narrow FP64 pipe would make costly):
-// [w_nu, w3, w4, rho0, urx, ury, Px0, Px+, Px-, Py0, Py+, Py-].
-constexpr int kNumConsts = 12;
+// [w_nu, w3, w4, rho0, urx, ury, Px0, Px+, Px-, Py0, Py+, Py-, urx^2 + cs^2, ury^2 + cs^2].
+constexpr int kNumConsts = 14;
 
 struct StepArgs {
     int nx, ny;          // lattice size
@@ -64,7 +64,8 @@ struct StepArgs {
 __host__ __device__ inline void fill_consts(StepArgs& a) {
     const double v[kNumConsts] = {a.w_nu, a.w3, a.w4, a.rho0, a.urx, a.ury,
                                   phi1d(0, a.urx), phi1d(1, a.urx), phi1d(-1, a.urx),
-                                  phi1d(0, a.ury), phi1d(1, a.ury), phi1d(-1, a.ury)};
+                                  phi1d(0, a.ury), phi1d(1, a.ury), phi1d(-1, a.ury),
+                                  a.urx * a.urx + 1.0 / 3.0, a.ury * a.ury + 1.0 / 3.0};
     for (int k = 0; k < kNumConsts; ++k) {
         a.cd[k] = v[k];
         a.cf[k] = (float)v[k];
@@ -167,6 +168,7 @@ __device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
 template <typename T> struct Consts {
     T w, w3, w4, rho0, urx, ury;
     T Px[3], Py[3];      // phi_s(u_ref) for s = 0, +1, -1 (shift factors)
+    T Xr, Yr;            // mu_2(u_ref) = u_ref^2 + c_s^2 per axis
 };
 template <typename T> __device__ __forceinline__ const T* const_table(const StepArgs& a);
 template <> __device__ __forceinline__ const float* const_table<float>(const StepArgs& a) { return a.cf; }
@@ -179,6 +181,7 @@ __device__ __forceinline__ Consts<T> make_consts(const StepArgs& a) {
     c.w = t[0]; c.w3 = t[1]; c.w4 = t[2]; c.rho0 = t[3]; c.urx = t[4]; c.ury = t[5];
     c.Px[0] = t[6]; c.Px[1] = t[7]; c.Px[2] = t[8];
     c.Py[0] = t[9]; c.Py[1] = t[10]; c.Py[2] = t[11];
+    c.Xr = t[12]; c.Yr = t[13];
     return c;
 }
 
@@ -186,25 +189,38 @@ __device__ __forceinline__ Consts<T> make_consts(const StepArgs& a) {
 // Per-node collision (App. B) on shifted populations g_i = f_i - s_i.
 //
 // Every model of App. B relaxes the moments of f towards those of f^eq with the same rho
-// and u, through a transform that is linear in f for the node's u.  So each model can be
-// written as f* = f^eq + T(u)^-1 [ (1 - omega_n) T(u) f^neq ] with f^neq = f - f^eq, where
-// the conserved (order 0 and 1) non-equilibrium moments are exactly zero.  Working with
-// f^neq and the deviation g^eq = f^eq - s keeps every intermediate small, which is what
-// makes FP32 arithmetic on FP16-stored populations accurate.  The cumulant model adds the
-// C22 product terms, the recursive regularized model the recursion of Eq. RRformulas_D2Q9.
-// rho, ux, uy of the pre-collision state are returned for diagnostics.  SHIFT = false is the
-// default shift s = w rho0 (u_ref = 0) with compile-time weights, which keeps the shift
-// constants out of registers.
+// and u, through a transform that is linear in f for the node's u, and keeps the conserved
+// moments (order 0 and 1).  So each model is f* = f - T(u)^-1 D with D = n - n*: n the
+// non-equilibrium moments M(f) - M^eq(rho, u), n* their post-collision values, and D's
+// conserved components exactly zero.  The kernels compute that directly on the stored
+// g = f - s: the nine raw moments of g by x-then-y partial sums; n = M(g) - (M^eq - M(s)),
+// where M^eq_pq = rho mu_p(u_x) mu_q(u_y) and M_pq(s) = rho0 mu_p(ur_x) mu_q(ur_y) are the
+// product-form moments of Eq. extendedFeq (mu_0 = 1, mu_1 = u, mu_2 = u^2 + c_s^2), their
+// difference written without cancellation; the model's relaxation of n (raw, Hermite,
+// central, central-Hermite, cumulant, recursive); and g* = g - (back-transform of D, Eq.
+// Q9postCollVDF_RM with D_00 = D_10 = D_01 = 0).  BGK is the raw-moment relaxation with one
+// rate for every order (exact for the D2Q9 moment basis).  Every intermediate is small, which
+// is what makes FP32 arithmetic on FP16-stored populations accurate, and the stored mass and
+// momentum change only by the rounding of D.  rho, ux, uy of the pre-collision state are
+// returned for diagnostics.  SHIFT = false is the default shift s = w rho0 (u_ref = 0), which
+// keeps the shift constants out of the arithmetic.  EQ = 2 (BGK only) uses the second-order
+// equilibrium of Sec. 2 in population space.
 template <int MODEL, int EQ, typename T, bool SHIFT>
 __device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], const Consts<T>& c, T& rho_out, T& ux_out,
                                         T& uy_out) {
     const T cs2 = T(1) / T(3);
     const T w = c.w, w3 = c.w3, w4 = c.w4;
-    // density and velocity (Sec. 1): sum s_i = rho0, sum xi_i s_i = rho0 u_ref
-    const T drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    // x-sums of each row of the velocity set (xi_y = +1, 0, -1) with weights 1, xi_x, xi_x^2
+    const T a0p = (g[6] + g[2]) + g[5], a1p = g[5] - g[6], a2p = g[5] + g[6];
+    const T a0z = (g[3] + g[0]) + g[1], a1z = g[1] - g[3], a2z = g[1] + g[3];
+    const T a0m = (g[7] + g[4]) + g[8], a1m = g[8] - g[7], a2m = g[8] + g[7];
+    // raw moments of g (App. B, M_pq = sum xi_x^p xi_y^q g); sum s = rho0, sum xi s = rho0 u_ref
+    const T drho = (a0p + a0z) + a0m;
+    T jx = (a1p + a1z) + a1m;
+    T jy = a0p - a0m;
+    const T m20 = (a2p + a2z) + a2m, m02 = a0p + a0m, m11 = a1p - a1m;
+    const T m21 = a2p - a2m, m12 = a1p + a1m, m22 = a2p + a2m;
     const T rho = c.rho0 + drho;
-    T jx = (g[1] - g[3]) + ((g[5] - g[7]) + (g[8] - g[6]));
-    T jy = (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
     if (SHIFT) {
         jx += c.rho0 * c.urx;
         jy += c.rho0 * c.ury;
@@ -214,147 +230,127 @@ __device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], const Consts
     const T uxx = ux * ux, uyy = uy * uy;
     rho_out = rho; ux_out = ux; uy_out = uy;
 
-    // g^eq_i = f^eq_i - s_i
-    T geq[9];
-    if (EQ == 4) {
-        // Eq. extendedFeq, product form: f^eq_(sx,sy) = rho phi_sx(u_x) phi_sy(u_y), written as
-        // phi_s(u) = P_s + D_s with P_s = phi_s(u_ref) and the difference
-        // D_0 = -(u - ur)(u + ur), D_+-1 = (u - ur)((u + ur) +- 1) / 2:
-        // f^eq - s = drho P_a P_b + rho (P_a D_b + D_a (P_b + D_b))
-        T Dx0, Dxp, Dxm, Dy0, Dyp, Dym, Px0, Pxp, Pxm, Py0, Pyp, Pym;
-        if (SHIFT) {
-            const T dux = ux - c.urx, sux = ux + c.urx, duy = uy - c.ury, suy = uy + c.ury;
-            Dx0 = -dux * sux; Dxp = T(0.5) * (dux * (sux + T(1))); Dxm = T(0.5) * (dux * (sux - T(1)));
-            Dy0 = -duy * suy; Dyp = T(0.5) * (duy * (suy + T(1))); Dym = T(0.5) * (duy * (suy - T(1)));
-            Px0 = c.Px[0]; Pxp = c.Px[1]; Pxm = c.Px[2];
-            Py0 = c.Py[0]; Pyp = c.Py[1]; Pym = c.Py[2];
-        } else {
-            Dx0 = -uxx; Dxp = T(0.5) * (uxx + ux); Dxm = T(0.5) * (uxx - ux);
-            Dy0 = -uyy; Dyp = T(0.5) * (uyy + uy); Dym = T(0.5) * (uyy - uy);
-            Px0 = Py0 = T(2) / T(3);
-            Pxp = Pxm = Pyp = Pym = T(1) / T(6);
-        }
-        // f^eq - s = drho P_a P_b + P_a (rho D_b) + (rho D_a)(P_b + D_b)
-        const T Ex0 = rho * Dx0, Exp = rho * Dxp, Exm = rho * Dxm;
-        const T Ey0 = rho * Dy0, Eyp = rho * Dyp, Eym = rho * Dym;
-        const T Hy0 = Py0 + Dy0, Hyp = Pyp + Dyp, Hym = Pym + Dym;
-#define LBM_GEQ(Pa, Ea, Pb, Eb, Hb) (((Pa) * (Pb)) * drho + (Pa) * (Eb) + (Ea) * (Hb))
-        geq[0] = LBM_GEQ(Px0, Ex0, Py0, Ey0, Hy0);
-        geq[1] = LBM_GEQ(Pxp, Exp, Py0, Ey0, Hy0);
-        geq[2] = LBM_GEQ(Px0, Ex0, Pyp, Eyp, Hyp);
-        geq[3] = LBM_GEQ(Pxm, Exm, Py0, Ey0, Hy0);
-        geq[4] = LBM_GEQ(Px0, Ex0, Pym, Eym, Hym);
-        geq[5] = LBM_GEQ(Pxp, Exp, Pyp, Eyp, Hyp);
-        geq[6] = LBM_GEQ(Pxm, Exm, Pyp, Eyp, Hyp);
-        geq[7] = LBM_GEQ(Pxm, Exm, Pym, Eym, Hym);
-        geq[8] = LBM_GEQ(Pxp, Exp, Pym, Eym, Hym);
-#undef LBM_GEQ
-    } else {
+    if (EQ == 2) {
         // second-order equilibrium (Sec. 2, Hermite reading), shift s = w rho0 (u_ref = 0):
-        // f^eq_i = w_i rho (1 + 3 xi.u + 4.5 (xi.u)^2 - 1.5 u^2)
+        // f^eq_i = w_i rho (1 + 3 xi.u + 4.5 (xi.u)^2 - 1.5 u^2); BGK in population space
         const T usq = T(1.5) * (uxx + uyy);
+        const T cc = T(1) - w;
+        T fn[9], geq[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const T wi = T(weight_of(i));
             const T eu = T(3) * (T(ex_of(i)) * ux + T(ey_of(i)) * uy);
             geq[i] = wi * drho + wi * rho * (eu + T(0.5) * eu * eu - usq);
+            fn[i] = g[i] - geq[i];
         }
-    }
-
-    T fn[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fn[i] = g[i] - geq[i];
-
-    if (MODEL == BGK) {
-        // f^neq has no mass or momentum in exact arithmetic; in finite precision it carries
-        // their rounding, which f* = f^eq + (1 - omega) f^neq would feed back with a factor
-        // |1 - omega| ~ 1 at low viscosity.  Remove it (the moment-space models drop the same
-        // components), i.e. subtract the populations (e0, ex/2, -ex/2, ey/2, -ey/2) that carry
-        // exactly those moments and nothing else: the map is unchanged, its FP32 rounding is
-        // that of the moment-space models.
+        // f^neq carries the rounding of the conserved moments, which (1 - omega) would feed
+        // back with a factor ~1 at low viscosity: remove it (populations carrying exactly the
+        // residual mass and momentum), the map is unchanged
         const T e0 = ((fn[0] + fn[1]) + (fn[2] + fn[3])) + ((fn[4] + fn[5]) + (fn[6] + fn[7])) + fn[8];
         const T hx = T(0.5) * ((fn[1] - fn[3]) + ((fn[5] - fn[7]) + (fn[8] - fn[6])));
         const T hy = T(0.5) * ((fn[2] - fn[4]) + ((fn[5] - fn[7]) + (fn[6] - fn[8])));
         fn[0] -= e0;
         fn[1] -= hx; fn[3] += hx;
         fn[2] -= hy; fn[4] += hy;
-        const T cc = T(1) - w;
 #pragma unroll
         for (int i = 0; i < 9; ++i) o[i] = geq[i] + cc * fn[i];
         return;
     }
 
-    // raw moments of f^neq (App. B, M_pq = sum xi_x^p xi_y^q f), x sums then y sums
-    const T a0p = (fn[6] + fn[2]) + fn[5], a1p = fn[5] - fn[6], a2p = fn[5] + fn[6];
-    const T a0m = (fn[7] + fn[4]) + fn[8], a1m = fn[8] - fn[7], a2m = fn[8] + fn[7];
-    const T a2z = fn[1] + fn[3];
-    const T m20 = (a2m + a2z) + a2p, m02 = a0p + a0m, m11 = a1p - a1m;
-    const T m21 = a2p - a2m, m12 = a1p + a1m, m22 = a2p + a2m;
-
-    const T c2 = T(1) - w, c3 = T(1) - w3, c4 = T(1) - w4;
-    T M20, M02, M11, M21, M12, M22;   // post-collision non-equilibrium raw moments
-    if (MODEL == RM) {
-        // Eq. RMcoll
-        M20 = c2 * m20; M02 = c2 * m02; M11 = c2 * m11;
-        M21 = c3 * m21; M12 = c3 * m12; M22 = c4 * m22;
-    } else if (MODEL == HM || MODEL == PR) {
-        // Hermite moments: A_2 = M_2, A_21 = M_21, A_12 = M_12 (conserved parts vanish),
-        // A_22 = M_22 - c_s^2 (M_20 + M_02); back with Eq. HM2RM_Q9
-        M20 = c2 * m20; M02 = c2 * m02; M11 = c2 * m11;
-        if (MODEL == HM) {
-            M21 = c3 * m21; M12 = c3 * m12;
-            M22 = c4 * (m22 - cs2 * (m20 + m02)) + cs2 * (M20 + M02);
-        } else {   // PR: omega3 = omega4 = 1
-            M21 = T(0); M12 = T(0);
-            M22 = cs2 * (M20 + M02);
-        }
-    } else if (MODEL == RR) {
-        // Eqs. HMColl_Q9, RRformulas_D2Q9: third/fourth-order A^neq from the recursion
-        const T a21 = uy * m20 + T(2) * ux * m11;
-        const T a12 = ux * m02 + T(2) * uy * m11;
-        const T a22 = uyy * m20 + uxx * m02 + T(4) * ux * uy * m11;
-        M20 = c2 * m20; M02 = c2 * m02; M11 = c2 * m11;
-        M21 = c3 * a21; M12 = c3 * a12;
-        M22 = c4 * a22 + cs2 * (M20 + M02);
+    // non-equilibrium raw moments n = M(g) - (M^eq(rho, u) - M(s)) (Eq. extendedFeq)
+    T n20, n02, n11, n21, n12, n22;
+    if (SHIFT) {
+        const T X = uxx + cs2, Y = uyy + cs2;                   // mu_2(u_x), mu_2(u_y)
+        const T dx = ux - c.urx, dy = uy - c.ury;               // mu_1(u) - mu_1(u_ref)
+        const T dX = dx * (ux + c.urx), dY = dy * (uy + c.ury); // mu_2(u) - mu_2(u_ref)
+        const T r0 = c.rho0;
+        n20 = m20 - (drho * X + r0 * dX);
+        n02 = m02 - (drho * Y + r0 * dY);
+        n11 = m11 - (drho * (ux * uy) + r0 * (dx * uy + c.urx * dy));
+        n21 = m21 - (drho * (X * uy) + r0 * (dX * uy + c.Xr * dy));
+        n12 = m12 - (drho * (ux * Y) + r0 * (dx * Y + c.urx * dY));
+        n22 = m22 - (drho * (X * Y) + r0 * (dX * Y + c.Xr * dY));
     } else {
-        // central moments of f^neq: binomial shift by -u (first-order parts vanish)
-        const T k20 = m20, k02 = m02, k11 = m11;
-        const T k21 = m21 - T(2) * ux * m11 - uy * m20;
-        const T k12 = m12 - T(2) * uy * m11 - ux * m02;
-        const T k22 = m22 - T(2) * ux * m12 - T(2) * uy * m21 + uxx * m02 + uyy * m20 + T(4) * ux * uy * m11;
-        const T K20 = c2 * k20, K02 = c2 * k02, K11 = c2 * k11;
-        const T K21 = c3 * k21, K12 = c3 * k12;
-        T K22;
-        if (MODEL == CM) {
-            K22 = c4 * k22;
-        } else if (MODEL == CHM) {
-            // central Hermite: A~_22 = K~_22 - c_s^2 (K~_20 + K~_02)   (Eqs. CHpoly, CHMcoll)
-            K22 = c4 * (k22 - cs2 * (k20 + k02)) + cs2 * (K20 + K02);
-        } else {
-            // cumulants: C22 = K22 - (K20 K02 + 2 K11^2)/rho relaxes to 0; rebuilt with the
-            // post-collision second-order central moments (written for deviations from
-            // the equilibrium central moments rho c_s^2, 0, rho c_s^4)
-            const T C22 = k22 - cs2 * (k20 + k02) - (k20 * k02 + T(2) * k11 * k11) * irho;
-            K22 = c4 * C22 + cs2 * (K20 + K02) + (K20 * K02 + T(2) * K11 * K11) * irho;
-        }
-        // back to raw moments: binomial shift by +u
-        M20 = K20; M02 = K02; M11 = K11;
-        M21 = K21 + T(2) * ux * K11 + uy * K20;
-        M12 = K12 + T(2) * uy * K11 + ux * K02;
-        M22 = K22 + T(2) * ux * K12 + T(2) * uy * K21 + uxx * K02 + uyy * K20 + T(4) * ux * uy * K11;
+        const T Y = uyy + cs2;
+        const T rX = rho * (uxx + cs2);
+        n20 = m20 - (cs2 * drho + rho * uxx);
+        n02 = m02 - (cs2 * drho + rho * uyy);
+        n11 = m11 - rho * (ux * uy);
+        n21 = m21 - rX * uy;
+        n12 = m12 - (rho * ux) * Y;
+        n22 = m22 - (drho * ((uxx + cs2) * Y) + c.rho0 * (uxx * Y + cs2 * uyy));
     }
 
-    // Eq. Q9postCollVDF_RM with M00 = M10 = M01 = 0 (non-equilibrium part), added to g^eq
+    // D = n - n* (the moments the collision removes), per model
+    T D20, D02, D11, D21, D12, D22;
+    if (MODEL == BGK || MODEL == RM) {
+        // Eq. RMcoll (BGK: one rate for every order)
+        const T r3 = (MODEL == BGK) ? w : w3, r4 = (MODEL == BGK) ? w : w4;
+        D20 = w * n20; D02 = w * n02; D11 = w * n11;
+        D21 = r3 * n21; D12 = r3 * n12; D22 = r4 * n22;
+    } else if (MODEL == HM || MODEL == PR) {
+        // Hermite moments: A_2 = n_2, A_21 = n_21, A_12 = n_12 (conserved parts vanish),
+        // A_22 = n_22 - c_s^2 (n_20 + n_02); relaxed, back with Eq. HM2RM_Q9
+        D20 = w * n20; D02 = w * n02; D11 = w * n11;
+        if (MODEL == HM) {
+            D21 = w3 * n21; D12 = w3 * n12;
+            D22 = w4 * (n22 - cs2 * (n20 + n02)) + cs2 * (D20 + D02);
+        } else {   // PR: omega3 = omega4 = 1
+            D21 = n21; D12 = n12;
+            D22 = (n22 - cs2 * (n20 + n02)) + cs2 * (D20 + D02);
+        }
+    } else if (MODEL == RR) {
+        // Eqs. HMColl_Q9, RRformulas_D2Q9: third/fourth-order A^neq from the recursion,
+        // A* = A^eq + (1 - omega) A^neq_rec, so D = A^neq - (1 - omega) A^neq_rec
+        const T a21 = uy * n20 + T(2) * ux * n11;
+        const T a12 = ux * n02 + T(2) * uy * n11;
+        const T a22 = uyy * n20 + uxx * n02 + T(4) * ux * uy * n11;
+        const T c3 = T(1) - w3, c4 = T(1) - w4;
+        D20 = w * n20; D02 = w * n02; D11 = w * n11;
+        D21 = n21 - c3 * a21; D12 = n12 - c3 * a12;
+        D22 = (n22 - cs2 * (n20 + n02)) - c4 * a22 + cs2 * (D20 + D02);
+    } else {
+        // central moments of f^neq: binomial shift by -u (first-order parts vanish)
+        const T k21 = n21 - T(2) * ux * n11 - uy * n20;
+        const T k12 = n12 - T(2) * uy * n11 - ux * n02;
+        const T k22 = n22 - T(2) * ux * n12 - T(2) * uy * n21 + uxx * n02 + uyy * n20 + T(4) * ux * uy * n11;
+        // removed central moments d = k - k*
+        const T d20 = w * n20, d02 = w * n02, d11 = w * n11;
+        const T d21 = w3 * k21, d12 = w3 * k12;
+        T d22;
+        if (MODEL == CM) {
+            d22 = w4 * k22;
+        } else if (MODEL == CHM) {
+            // central Hermite: A~_22 = K~_22 - c_s^2 (K~_20 + K~_02)   (Eqs. CHpoly, CHMcoll)
+            d22 = w4 * (k22 - cs2 * (n20 + n02)) + cs2 * (d20 + d02);
+        } else {
+            // cumulants: C22 = K22 - (K20 K02 + 2 K11^2)/rho relaxes to 0 and K22* is rebuilt
+            // with the post-collision second-order central moments (written for deviations
+            // from the equilibrium central moments rho c_s^2, 0, rho c_s^4)
+            const T c2 = T(1) - w;
+            const T K20 = c2 * n20, K02 = c2 * n02, K11 = c2 * n11;
+            const T C22 = k22 - cs2 * (n20 + n02) - (n20 * n02 + T(2) * n11 * n11) * irho;
+            const T K22 = (T(1) - w4) * C22 + cs2 * (K20 + K02) + (K20 * K02 + T(2) * K11 * K11) * irho;
+            d22 = k22 - K22;
+        }
+        // back to raw moments: binomial shift by +u (linear, so it applies to d directly)
+        D20 = d20; D02 = d02; D11 = d11;
+        D21 = d21 + T(2) * ux * d11 + uy * d20;
+        D12 = d12 + T(2) * uy * d11 + ux * d02;
+        D22 = d22 + T(2) * ux * d12 + T(2) * uy * d21 + uxx * d02 + uyy * d20 + T(4) * ux * uy * d11;
+    }
+
+    // g* = g - (Eq. Q9postCollVDF_RM applied to D, with D_00 = D_10 = D_01 = 0)
     const T h = T(0.5), q = T(0.25);
-    o[0] = geq[0] + (M22 - (M20 + M02));
-    o[1] = geq[1] + h * ((M20 - M22) - M12);
-    o[3] = geq[3] + h * ((M20 - M22) + M12);
-    o[2] = geq[2] + h * ((M02 - M22) - M21);
-    o[4] = geq[4] + h * ((M02 - M22) + M21);
-    o[5] = geq[5] + q * ((M22 + M11) + (M12 + M21));
-    o[6] = geq[6] + q * ((M22 - M11) + (M21 - M12));
-    o[7] = geq[7] + q * ((M22 + M11) - (M12 + M21));
-    o[8] = geq[8] + q * ((M22 - M11) + (M12 - M21));
+    o[0] = g[0] - (D22 - (D20 + D02));
+    o[1] = g[1] - h * ((D20 - D22) - D12);
+    o[3] = g[3] - h * ((D20 - D22) + D12);
+    o[2] = g[2] - h * ((D02 - D22) - D21);
+    o[4] = g[4] - h * ((D02 - D22) + D21);
+    o[5] = g[5] - q * ((D22 + D11) + (D12 + D21));
+    o[6] = g[6] - q * ((D22 - D11) + (D21 - D12));
+    o[7] = g[7] - q * ((D22 + D11) - (D12 + D21));
+    o[8] = g[8] - q * ((D22 - D11) + (D12 - D21));
 }
 
 // Per-thread FP64 accumulators of the blow-up diagnostics (used by the batched sweep).

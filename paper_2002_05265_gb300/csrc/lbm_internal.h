@@ -71,8 +71,8 @@ struct AdjArgs {
     long long plane;
     double w_nu, w3, w4, rho0;
     double urx, ury;     // storage shift velocity
-    double cd[12];       // collision constants as in StepArgs (fill_consts), FP64 and FP32
-    float cf[12];
+    double cd[16];       // collision constants as in StepArgs (fill_consts), FP64 and FP32
+    float cf[16];
 };
 struct AdjointPlan {
     int storage;            // LBM_F64 or LBM_F32 (lambda kept in the collision precision)

@@ -19,9 +19,36 @@
 // multiple of 32 elements).  Pull: node x of the tile reads element x - xi_ix of its
 // plane's slot, one element left or right of its own vector.
 //
+// Several time steps per launch: tile t of step s is the global work item s * T + t (T tiles
+// per step), and CTA b takes items b, b + grid, ... in order.  A tile of step s >= 1 may be
+// copied only when the rows it pulls from (its own and the neighbouring rows or row blocks)
+// are complete in step s - 1.  A signal warp (one lane) follows the consumers: each consumer
+// warp, after its stores, adds one to its stage's completion count in shared memory (release
+// at CTA scope); when the count shows all eight warps done with a tile, the signal lane
+// issues a GPU-scope fence (cumulative over those stores) and adds one to the tile's per-row
+// (per row-block) counter in global memory.  It runs beside the copy pipeline, never gating
+// it: the producer reuses a stage as soon as the consumers release it (mbarrier `empty`),
+// and the stage counts are monotone, so the signal lane may lag.  The producer reads the
+// counters it needs with overlapped relaxed loads, then one acquire fence and one
+// async-proxy fence, before it waits for a free stage and issues the copies; the consumers
+// never wait on memory fences.  That condition also covers the buffer reuse: the
+// rows a tile overwrites were last read by exactly those step s - 1 tiles.  Dependencies
+// point to smaller work items only, and the grid is launched cooperatively (all CTAs
+// resident), so the waits always end.
+//
+// Wavefront order (lattices of one geometry): the steps of a launch are interleaved so that
+// a unit (row or row block) is advanced again a few units behind the front of the previous
+// step, while what that step wrote is still in the L2; the intermediate states then never
+// reach HBM (rows are overwritten two steps later while still resident), and a launch of K
+// steps moves about one read and two writes of the populations through HBM instead of K of
+// each.  Step s visits the units in the order u = (j + s) mod U, j = 0, 1, ..., and unit
+// index j of step s is ordered at key j + s * D: the units a tile pulls from in step s - 1
+// have j' in {j, j + 1, j + 2} (mod U), so with D >= 3 every dependency has a smaller key,
+// across the periodic wrap too.
+//
 // Stage layout (per population i): [16-byte left chunk][W elements][16-byte right chunk].
 // Barriers: full[s] (one producer arrival plus the copies' byte count) and empty[s] (one
-// arrival per consumer warp).  Every wait is bounded: after about two seconds of waiting a
+// arrival per consumer warp); done[s] counts the consumer warps' completed tiles of stage s.  Every wait is bounded: after about two seconds of waiting a
 // thread sets the caller's flag, and the producer first lets its own copies land.
 #pragma once
 
@@ -30,7 +57,7 @@
 namespace lbm {
 
 constexpr int kTileConsumerWarps = 8;
-constexpr int kTileThreads = (kTileConsumerWarps + 1) * 32;
+constexpr int kTileThreads = (kTileConsumerWarps + 2) * 32;   // + producer warp + signal warp
 
 // Nodes a consumer thread collides per pass (one vector access per population): 16 bytes
 // for FP64/FP32; for the 16-bit types LBM_TILE_HALF_CV nodes (4 = 8-byte accesses in two
@@ -48,8 +75,11 @@ template <typename S> struct Tile {
 };
 
 struct TileEntry {
-    const void* src;    // buffers of the storage type of the launch
-    void* dst;
+    const void* buf[2]; // the lattice's two buffers (storage type of the launch): time step s of
+    int cur;            // the launch reads buf[(cur + s) & 1] and writes buf[(cur + s + 1) & 1];
+    long long ring;     // or, when ring > 0, reads buf[0] + s * ring and writes buf[0] + (s + 1) * ring
+                        // (elements; the recomputed states of the adjoint)
+    unsigned cbase;     // first completion counter of this lattice (one per row or row block)
     StepArgs a;
     int model;          // lbm::Model
     int eq_order;       // 4, or 2 (BGK only)
@@ -59,8 +89,16 @@ struct TileEntry {
 };
 struct TileArgs {
     int n;              // lattices
-    unsigned total;     // tiles of all lattices
+    unsigned total;     // tiles of all lattices in one time step
+    int nsteps;         // time steps of the launch
     int* flag;          // device int set to 1 when a wait gives up
+    unsigned* cnt;      // completion counters, zero at launch (used when nsteps > 1)
+    // Work-item order.  wave = 0: step-major (item s * total + t).  wave = 1 (lattices of one
+    // geometry: wU units of wntx tiles each): wavefront, item ((k * nsteps + s) * n + e) * wntx
+    // + x is segment x of unit u = (k - s * wD + s) mod wU of lattice e at step s, valid when
+    // 0 <= k - s * wD < wU; witems items in all.
+    int wave, wU, wntx, wD;
+    unsigned witems;
     TileEntry e[kGroupMax];
 };
 
@@ -106,6 +144,39 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         if ((it & 1023u) == 0 && it > (1u << 20) && global_ns() - t0 > 2000000000ull) return false;
     }
 }
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void smem_add_release(unsigned* p, unsigned v) {
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned smem_ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_add_relaxed(unsigned* p, unsigned v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// orders this thread's generic-proxy global accesses with its bulk (async-proxy) copies
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Waits until all three counters are >= need (relaxed loads, issued together); the caller
+// then fences.  False after about two seconds (and at least 2^20 polls).
+__device__ __forceinline__ bool counters_wait(const unsigned* a, const unsigned* b, const unsigned* c,
+                                              unsigned need) {
+    uint64_t t0 = 0;
+    for (uint64_t it = 0;; ++it) {
+        const unsigned va = ld_relaxed(a), vb = ld_relaxed(b), vc = ld_relaxed(c);
+        if (va >= need && vb >= need && vc >= need) return true;
+        if (it == 0) t0 = global_ns();
+        if ((it & 1023u) == 1023u && it > (1u << 20) && global_ns() - t0 > 2000000000ull) return false;
+    }
+}
 // global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned),
 // completing on the transaction count of `bar`
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -121,6 +192,7 @@ struct TilePos {
     int x0;     // first node of the row segment (0 for row-block tiles)
     int w;      // nodes per row in the tile
     int rows;   // rows in the tile (1 for segment tiles)
+    int unit;   // completion counter of the tile within its lattice: row, or row block
 };
 template <typename S>
 __device__ __forceinline__ TilePos tile_pos(const TileArgs& g, unsigned t) {
@@ -135,18 +207,45 @@ __device__ __forceinline__ TilePos tile_pos(const TileArgs& g, unsigned t) {
         q.x0 = (int)(lt - (unsigned)q.y * (unsigned)E.ntx) * Tile<S>::W;
         q.w = min(Tile<S>::W, E.a.nx - q.x0);
         q.rows = 1;
+        q.unit = q.y;
     } else {
         q.y = (int)lt * E.rows;
         q.x0 = 0;
         q.w = E.a.nx;
         q.rows = min(E.rows, E.a.ny - q.y);
+        q.unit = (int)lt;
     }
     return q;
 }
 
+// Work item i -> (step, tile of the step); false for the padding items of the wavefront order.
+__device__ __forceinline__ bool item_at(const TileArgs& g, unsigned i, int& step, unsigned& t) {
+    if (!g.wave) {
+        step = (int)(i / g.total);
+        t = i - (unsigned)step * g.total;
+        return true;
+    }
+    const unsigned x = i % (unsigned)g.wntx;
+    i /= (unsigned)g.wntx;
+    const unsigned e = i % (unsigned)g.n;
+    i /= (unsigned)g.n;
+    const int s = (int)(i % (unsigned)g.nsteps);
+    const int j = (int)(i / (unsigned)g.nsteps) - s * g.wD;
+    if (j < 0 || j >= g.wU) return false;
+    const unsigned u = (unsigned)(j + s % g.wU) % (unsigned)g.wU;
+    const TileEntry& E = g.e[e];
+    step = s;
+    t = E.begin + (E.ntx > 0 ? u * (unsigned)E.ntx + x : u);
+    return true;
+}
+__device__ __forceinline__ unsigned item_count(const TileArgs& g) {
+    return g.wave ? g.witems : (unsigned)g.nsteps * g.total;
+}
+
 // ---- consumer: collide VEC nodes of a staged tile --------------------------------------------
 template <int MODEL, int EQ, typename S, bool SHIFT>
-__device__ __forceinline__ void tile_collide(const unsigned char* stage, const TileEntry& E, const TilePos& q, int p) {
+__device__ __forceinline__ void tile_collide(const unsigned char* stage, S* dstbuf, const TileEntry& E, const TilePos& q,
+                                             int p) {
     using T = typename Conv<S>::T;
     constexpr int VEC = Tile<S>::VEC;
     const Consts<T> c = make_consts<T>(E.a);
@@ -189,25 +288,26 @@ __device__ __forceinline__ void tile_collide(const unsigned char* stage, const T
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i][j] = gout[i];
     }
-    S* dst = static_cast<S*>(E.dst) + (long long)(q.y + r) * E.a.pitch + q.x0 + x;
+    S* dst = dstbuf + (long long)(q.y + r) * E.a.pitch + q.x0 + x;
 #pragma unroll
     for (int i = 0; i < 9; ++i) vstore<S, VEC>(dst + (long long)i * E.a.plane, out[i]);
 }
 
 template <typename S, bool SHIFT>
-__device__ __forceinline__ void tile_consume(const unsigned char* stage, const TileEntry& E, const TilePos& q, int p) {
+__device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst, const TileEntry& E, const TilePos& q,
+                                             int p) {
     switch (E.model) {
         case BGK:
-            if (E.eq_order == 2) tile_collide<BGK, 2, S, SHIFT>(stage, E, q, p);
-            else tile_collide<BGK, 4, S, SHIFT>(stage, E, q, p);
+            if (E.eq_order == 2) tile_collide<BGK, 2, S, SHIFT>(stage, dst, E, q, p);
+            else tile_collide<BGK, 4, S, SHIFT>(stage, dst, E, q, p);
             break;
-        case RM: tile_collide<RM, 4, S, SHIFT>(stage, E, q, p); break;
-        case HM: tile_collide<HM, 4, S, SHIFT>(stage, E, q, p); break;
-        case CM: tile_collide<CM, 4, S, SHIFT>(stage, E, q, p); break;
-        case CHM: tile_collide<CHM, 4, S, SHIFT>(stage, E, q, p); break;
-        case CUM: tile_collide<CUM, 4, S, SHIFT>(stage, E, q, p); break;
-        case PR: tile_collide<PR, 4, S, SHIFT>(stage, E, q, p); break;
-        default: tile_collide<RR, 4, S, SHIFT>(stage, E, q, p); break;
+        case RM: tile_collide<RM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+        case HM: tile_collide<HM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+        case CM: tile_collide<CM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+        case CHM: tile_collide<CHM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+        case CUM: tile_collide<CUM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+        case PR: tile_collide<PR, 4, S, SHIFT>(stage, dst, E, q, p); break;
+        default: tile_collide<RR, 4, S, SHIFT>(stage, dst, E, q, p); break;
     }
 }
 
@@ -215,38 +315,96 @@ __device__ __forceinline__ void tile_consume(const unsigned char* stage, const T
 // Persistent: CTA b processes tiles b, b + gridDim.x, ...; warp 8 is the producer (one
 // lane issues the copies), warps 0-7 consume.  NS = stages in the ring.
 template <typename S, bool SHIFT, int NS>
-__global__ void __launch_bounds__(kTileThreads, 1) tile_step_kernel(const __grid_constant__ TileArgs g) {
+__global__ void __launch_bounds__(kTileThreads, sizeof(S) == 8 ? 1 : 2) tile_step_kernel(const __grid_constant__ TileArgs g) {
     using TS = Tile<S>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * TS::STAGE);
     uint64_t* empty = full + NS;
+    unsigned* done = reinterpret_cast<unsigned*>(empty + NS);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_addr(&full[s]), 1);
             mbar_init(smem_addr(&empty[s]), kTileConsumerWarps);
+            done[s] = 0u;
         }
         mbar_init_fence();
     }
     __syncthreads();
+    // CTA b takes work items b, b + gridDim.x, ... (all three roles in the same order)
+    const unsigned items = item_count(g);
+
+    if (warp == kTileConsumerWarps + 1) {
+        if (lane != 0 || g.nsteps == 1) return;   // a single-step launch has no dependencies
+        // ---------------- signal ----------------
+        int k = 0;
+        for (unsigned i = blockIdx.x; i < items; i += gridDim.x) {
+            int step;
+            unsigned t;
+            if (!item_at(g, i, step, t)) continue;
+            const int st = k % NS;
+            const unsigned need = (unsigned)kTileConsumerWarps * (unsigned)(k / NS + 1);
+            // all consumer warps done with this tile (monotone count: lagging is harmless)
+            bool ok = smem_ld_acquire(&done[st]) >= need;
+            if (!ok) {
+                const uint64_t w0 = global_ns();
+                for (uint64_t it = 0; !ok; ++it) {
+                    __nanosleep(64);
+                    ok = smem_ld_acquire(&done[st]) >= need;
+                    if (!ok && (it & 255u) == 255u && it > (1u << 16) && global_ns() - w0 > 2000000000ull) break;
+                }
+            }
+            if (!ok) {
+                atomicExch(g.flag, 1);
+                return;
+            }
+            if (step + 1 < g.nsteps) {
+                const TilePos q = tile_pos<S>(g, t);
+                fence_acq_rel_gpu();   // the consumers' stores, ordered before by the count
+                red_add_relaxed(g.cnt + g.e[q.e].cbase + q.unit, 1u);
+            }
+            ++k;
+        }
+        return;
+    }
 
     if (warp == kTileConsumerWarps) {
         if (lane != 0) return;
         // ---------------- producer ----------------
         int k = 0;
         bool ok = true;
-        for (unsigned t = blockIdx.x; t < g.total; t += gridDim.x, ++k) {
+        for (unsigned i = blockIdx.x; i < items; i += gridDim.x) {
+            int step;
+            unsigned t;
+            if (!item_at(g, i, step, t)) continue;
             const int st = k % NS;
             const uint32_t ph = (uint32_t)(k / NS) & 1u;
+            const TilePos q = tile_pos<S>(g, t);
+            const TileEntry& E = g.e[q.e];
+            const int nx = E.a.nx, ny = E.a.ny;
+            if (step > 0) {
+                // the rows this tile pulls from must be complete in the previous step (checked
+                // before waiting for the stage, so the counter latency overlaps the consumers)
+                const int units = E.ntx > 0 ? ny : (ny + E.rows - 1) / E.rows;
+                const unsigned need = (unsigned)step * (unsigned)(E.ntx > 0 ? E.ntx : 1);
+                const int um = q.unit == 0 ? units - 1 : q.unit - 1;
+                const int up = q.unit == units - 1 ? 0 : q.unit + 1;
+                const unsigned* c = g.cnt + E.cbase;
+                if (!counters_wait(c + um, c + q.unit, c + up, need)) {
+                    ok = false;
+                    break;
+                }
+                fence_acq_rel_gpu();          // acquire: the rows' stores happen before the copies
+                fence_proxy_async_global();   // ... including for the copy engine's reads
+            }
+            // a free stage: every consumer warp has released it
             if (k >= NS && !mbar_wait(smem_addr(&empty[st]), ph ^ 1u)) {
                 ok = false;
                 break;
             }
-            const TilePos q = tile_pos<S>(g, t);
-            const TileEntry& E = g.e[q.e];
-            const int nx = E.a.nx, ny = E.a.ny;
             const uint32_t bar = smem_addr(&full[st]);
-            const S* src = static_cast<const S*>(E.src);
+            const S* src = E.ring > 0 ? static_cast<const S*>(E.buf[0]) + (long long)step * E.ring
+                                      : static_cast<const S*>(E.buf[(E.cur + step) & 1]);
             const uint32_t sb = smem_addr(smem + st * TS::STAGE);
             const uint32_t row_bytes = (uint32_t)(q.w * (int)sizeof(S));
             if (E.ntx > 0) {
@@ -257,31 +415,31 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_step_kernel(const __grid
                 const int xl = (q.x0 == 0) ? nx - TS::H : q.x0 - TS::H;     // chunk ending at x0 - 1
                 const int xr = (q.x0 + q.w >= nx) ? 0 : q.x0 + q.w;        // chunk starting at x0 + w
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const int row = (ey_of(i) == 1) ? ym : ((ey_of(i) == -1) ? yp : q.y);
-                    const S* r = src + (long long)i * E.a.plane + (long long)row * E.a.pitch;
-                    const uint32_t slot = sb + i * TS::PLANE;
+                for (int pi = 0; pi < 9; ++pi) {
+                    const int row = (ey_of(pi) == 1) ? ym : ((ey_of(pi) == -1) ? yp : q.y);
+                    const S* r = src + (long long)pi * E.a.plane + (long long)row * E.a.pitch;
+                    const uint32_t slot = sb + pi * TS::PLANE;
                     bulk_g2s(slot + 16, r + q.x0, row_bytes, bar);
-                    if (ex_of(i) == 1) bulk_g2s(slot, r + xl, 16, bar);
-                    if (ex_of(i) == -1) bulk_g2s(slot + 16 + row_bytes, r + xr, 16, bar);
+                    if (ex_of(pi) == 1) bulk_g2s(slot, r + xl, 16, bar);
+                    if (ex_of(pi) == -1) bulk_g2s(slot + 16 + row_bytes, r + xr, 16, bar);
                 }
             } else {
                 // row-block tile: rows y - xi_iy of every population, consecutive rows merged
                 mbar_arrive_expect_tx(bar, 9 * (uint32_t)q.rows * row_bytes);
                 const bool dense = E.a.pitch == nx;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const S* pl = src + (long long)i * E.a.plane;
-                    const uint32_t slot = sb + i * TS::PLANE + 16;
+                for (int pi = 0; pi < 9; ++pi) {
+                    const S* pl = src + (long long)pi * E.a.plane;
+                    const uint32_t slot = sb + pi * TS::PLANE + 16;
                     int r = 0;
                     while (r < q.rows) {
-                        int row = q.y + r - ey_of(i);
+                        int row = q.y + r - ey_of(pi);
                         row = row < 0 ? row + ny : (row >= ny ? row - ny : row);
                         int run = 1;
                         if (dense) {
                             const int lim = min(q.rows - r, ny - row);   // stay inside the plane
                             while (run < lim) {
-                                int nr = q.y + r + run - ey_of(i);
+                                int nr = q.y + r + run - ey_of(pi);
                                 nr = nr < 0 ? nr + ny : (nr >= ny ? nr - ny : nr);
                                 if (nr != row + run) break;
                                 ++run;
@@ -292,6 +450,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_step_kernel(const __grid
                     }
                 }
             }
+            ++k;
         }
         if (!ok) {
             atomicExch(g.flag, 1);
@@ -304,10 +463,16 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_step_kernel(const __grid
 
     // ---------------- consumers ----------------
     int k = 0;
-    for (unsigned t = blockIdx.x; t < g.total; t += gridDim.x, ++k) {
+    for (unsigned i = blockIdx.x; i < items; i += gridDim.x) {
+        int step;
+        unsigned t;
+        if (!item_at(g, i, step, t)) continue;
         const int st = k % NS;
         const uint32_t ph = (uint32_t)(k / NS) & 1u;
         const TilePos q = tile_pos<S>(g, t);
+        const TileEntry& E = g.e[q.e];
+        S* dst = E.ring > 0 ? static_cast<S*>(const_cast<void*>(E.buf[0])) + (long long)(step + 1) * E.ring
+                            : static_cast<S*>(const_cast<void*>(E.buf[(E.cur + step + 1) & 1]));
         // every lane waits (acquiring the copied bytes); the warp leaves together on a timeout
         const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&full[st]), ph));
         if (!ok) {
@@ -317,14 +482,18 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_step_kernel(const __grid
 #pragma unroll
         for (int pass = 0; pass < TS::PASSES; ++pass) {
             const int p = (pass * kTileConsumerWarps * 32 + (int)threadIdx.x) * TS::VEC;
-            if (p < q.w * q.rows) tile_consume<S, SHIFT>(smem + st * TS::STAGE, g.e[q.e], q, p);
+            if (p < q.w * q.rows) tile_consume<S, SHIFT>(smem + st * TS::STAGE, dst, E, q, p);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
+        if (lane == 0) {
+            if (g.nsteps > 1) smem_add_release(&done[st], 1u);   // for the signal warp
+            mbar_arrive(smem_addr(&empty[st]));
+        }
+        ++k;
     }
 }
 
 // dynamic shared memory of tile_step_kernel<S, *, NS>
-template <typename S> constexpr int tile_smem_bytes(int ns) { return ns * Tile<S>::STAGE + 2 * ns * 8; }
+template <typename S> constexpr int tile_smem_bytes(int ns) { return ns * Tile<S>::STAGE + 2 * ns * 8 + ns * 4; }
 
 }  // namespace lbm

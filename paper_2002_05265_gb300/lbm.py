@@ -17,6 +17,7 @@ LBM_BGK, LBM_RM, LBM_HM, LBM_CM, LBM_CHM, LBM_K, LBM_PR, LBM_RR = range(8)
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = range(4)
 LBM_PRESET_SRT, LBM_PRESET_REG = 0, 1
 LBM_PATH_AUTO, LBM_PATH_VECTOR, LBM_PATH_BULK = 0, 1, 2
+LBM_ORDER_AUTO, LBM_ORDER_STEP, LBM_ORDER_WAVE = 0, 1, 2
 LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_CUDA, LBM_ERR_BLOWUP, LBM_ERR_TIMEOUT, LBM_ERR_NOMEM = \
     0, -1, -2, -3, -4, -5, -6
 
@@ -68,6 +69,7 @@ _SIGNATURES = {
     "lbm_synchronize": (_I, [_P]),
     "lbm_get_layout": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "lbm_set_kernel_path": (_I, [_P, _I, _I]),
+    "lbm_set_launch_shape": (_I, [_P, _I, _I]),
     "lbm_group_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _I]),
     "lbm_group_step": (_I, [_P, _LL]),
     "lbm_group_destroy": (None, [_P]),
@@ -217,6 +219,10 @@ def lbm_get_layout(ctx):
 
 def lbm_set_kernel_path(ctx, path, stages=0):
     _check(load_library().lbm_set_kernel_path(ctx, path, stages), ctx)
+
+
+def lbm_set_launch_shape(ctx, steps_per_launch=0, order=LBM_ORDER_AUTO):
+    _check(load_library().lbm_set_launch_shape(ctx, steps_per_launch, order), ctx)
 
 
 def lbm_group_create(ctxs, graph_steps=64):
@@ -391,3 +397,6 @@ class Lattice:
 
     def set_kernel_path(self, path, stages=0):
         lbm_set_kernel_path(self.ctx, path, stages)
+
+    def set_launch_shape(self, steps_per_launch=0, order=LBM_ORDER_AUTO):
+        lbm_set_launch_shape(self.ctx, steps_per_launch, order)

@@ -183,3 +183,108 @@ def test_bulk_row_block_tiles_reduced_precision(L, storage, shape):
         bound = 5e-3 if storage == "f16" else 4e-2
         assert _l2(bulk, ref) <= bound
         assert _l2(bulk, vec) <= bound
+
+
+def test_bulk_single_step_launches_large_lattice(L):
+    """A lattice with many tiles per CTA (16384 x 2048 FP32: 32768 tiles per step) runs one
+    time step per bulk-copy launch; smaller ones run many steps per launch with the
+    row-completion counters (every other test here).  After 12 steps of the CHM model on the
+    double shear layer: populations within 1e-6 of the register-staged kernels everywhere,
+    and 16 sampled nodes within 1e-5 of the oracle run on the light cone of each node."""
+    nx, ny, k = 16384, 2048, 12
+    fields = flows.double_shear_layer(nx, ny, Ma=0.1, width_frac=1.0 / 80.0)
+    rates = olbm.rates_from_nu(1e-5, "reg")
+    outs = []
+    for path in (L.LBM_PATH_BULK, L.LBM_PATH_VECTOR):
+        lat = L.Lattice(nx, ny, L.LBM_CHM, rates, storage=L.LBM_F32)
+        lat.set_kernel_path(path)
+        lat.init_equilibrium(*_dev(*fields))
+        lat.step(k)
+        assert lat.status()[0] == L.LBM_OK
+        ux = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+        uy = torch.empty_like(ux)
+        lat.moments(None, ux, uy)
+        outs.append((ux.cpu().numpy(), uy.cpu().numpy()))
+        lat.close()
+    (bx, by), (vx, vy) = outs
+    assert max(np.max(np.abs(bx - vx)), np.max(np.abs(by - vy))) <= 1e-6
+    g = np.random.default_rng(11)
+    pts = list(zip(g.integers(0, ny, 14), g.integers(0, nx, 14))) + [(0, 0), (ny - 1, nx - 1)]
+    P = 2 * k + 3
+    for (y, x) in pts:
+        ys = (np.arange(P) + y - P // 2) % ny
+        xs = (np.arange(P) + x - P // 2) % nx
+        patch = [a[np.ix_(ys, xs)] for a in fields]
+        fr = olbm.run(olbm.init_equilibrium(*patch), "chm", rates, k)
+        _, rx, ry = macroscopic(fr)
+        assert abs(bx[y, x] - rx[P // 2, P // 2]) <= 1e-5
+        assert abs(by[y, x] - ry[P // 2, P // 2]) <= 1e-5
+
+
+def _run_shaped(L, fields, model, rates, storage, steps, launch_steps, order):
+    rho, ux, uy = fields
+    ny, nx = rho.shape
+    lat = L.Lattice(nx, ny, L.MODELS[model], rates, storage=storage)
+    lat.set_kernel_path(L.LBM_PATH_BULK)
+    lat.set_launch_shape(launch_steps, order)
+    lat.init_equilibrium(*_dev(rho, ux, uy))
+    lat.step(steps)
+    assert lat.status()[0] == L.LBM_OK
+    f = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+    lat.get_populations(f)
+    lat.close()
+    return f.cpu().numpy()
+
+
+@pytest.mark.parametrize("model", ["bgk", "chm", "k", "rr"])
+@pytest.mark.parametrize("shape,launch_steps", [((1030, 6), 8), ((1030, 6), 3), ((64, 37), 7), ((70, 9), 16)])
+def test_wavefront_order_fp64(L, model, shape, launch_steps):
+    """Several time steps per launch in the wavefront order (steps interleaved a few rows
+    apart, units visited in a rotated order per step, across the periodic wrap): segment tiles
+    (1030 x 6) and row-block tiles (64 x 37, 70 x 9), 40 steps: within 1e-12 of the oracle."""
+    nx, ny = shape
+    fields = flows.vortex(nx, ny, Ma=0.3, radius_frac=0.05, noise=1e-6, seed=nx + ny + launch_steps)
+    rates = olbm.rates_from_nu(1e-3, "reg" if model in ("chm", "k") else "srt")
+    got = _run_shaped(L, fields, model, rates, L.LBM_F64, 40, launch_steps, L.LBM_ORDER_WAVE)
+    ref = olbm.run(olbm.init_equilibrium(*fields), model, rates, 40)
+    assert float(np.max(np.abs(got - ref) / np.abs(ref))) <= 1e-12
+
+
+def test_launch_shapes_agree_bitwise(L):
+    """The launch shape only reorders the same per-tile arithmetic: one step per launch, step
+    order with 10 steps per launch, and the wavefront with 16 steps per launch give identical
+    FP32 populations (eight 256 x 160 lattices of all models in one group, 50 steps)."""
+    rates = olbm.rates_from_nu(1e-4, "reg")
+    fields = flows.double_shear_layer(256, 160, Ma=0.1, width_frac=0.05)
+    results = []
+    for steps, order in ((1, L.LBM_ORDER_STEP), (10, L.LBM_ORDER_STEP), (16, L.LBM_ORDER_WAVE)):
+        lats = []
+        for m in MODELS:
+            lat = L.Lattice(256, 160, L.MODELS[m], rates, storage=L.LBM_F32)
+            lat.set_kernel_path(L.LBM_PATH_BULK)
+            lat.set_launch_shape(steps, order)
+            lat.init_equilibrium(*_dev(*fields))
+            lats.append(lat)
+        g = L.lbm_group_create([x.ctx for x in lats], graph_steps=8)
+        L.lbm_group_step(g, 50)
+        out = []
+        for lat in lats:
+            f = torch.empty((9, 160, 256), dtype=torch.float64, device="cuda")
+            lat.get_populations(f)
+            assert lat.status()[0] == L.LBM_OK
+            out.append(f)
+        results.append(torch.stack(out))
+        L.lbm_group_destroy(g)
+        for lat in lats:
+            lat.close()
+    assert torch.equal(results[0], results[1])
+    assert torch.equal(results[0], results[2])
+
+
+def test_launch_shape_argument_checks(L):
+    lat = L.Lattice(64, 64, L.LBM_BGK, (1.5, 1.5, 1.5), storage=L.LBM_F32)
+    for steps, order in ((-1, 0), (0, 3), (0, -1)):
+        with pytest.raises(L.LBMError) as e:
+            lat.set_launch_shape(steps, order)
+        assert e.value.code == L.LBM_ERR_INVALID_ARG
+    lat.close()
