@@ -195,7 +195,8 @@ int lbm_get_layout(const lbm_ctx* ctx, int* pitch, int* grid, int* block);
  *                    segments into a ring of `stages` (2-4; 0 = default) shared-memory stages
  *                    on mbarriers while eight consumer warps collide earlier tiles; needs
  *                    nx * (bytes per population) to be a multiple of 16.
- *   LBM_PATH_AUTO    BULK where the row length allows it, else VECTOR (the default).
+ *   LBM_PATH_AUTO    BULK where the row length allows it and a time step has at least one
+ *                    tile per resident CTA, else VECTOR (the default).
  * Applies to the context's next lbm_step and to groups created afterwards.  Errors:
  * LBM_ERR_INVALID_ARG for an unknown path or stage count, LBM_ERR_UNSUPPORTED for BULK on a
  * lattice whose rows are not a multiple of 16 bytes. */
@@ -206,15 +207,16 @@ int lbm_set_kernel_path(lbm_ctx* ctx, int path, int stages);
  * counterpart; results are identical for every shape).  One launch may advance several time
  * steps: a tile of step s is copied once the rows it pulls from are complete in step s - 1
  * (row-completion counters in device memory, cooperative launch).
- *   steps_per_launch  time steps per launch; 0 = default (16 with the wavefront order, many
- *                     for lattices with few tiles per CTA, else 1).
+ *   steps_per_launch  time steps per launch; 0 = default (16 with the wavefront order; else
+ *                     many when a step has fewer than 64 tiles per CTA, 1 otherwise).
  *   order             LBM_ORDER_STEP: every tile of step s before those of step s + 1 (in
  *                     the CTAs' round-robin).  LBM_ORDER_WAVE (lattices of one geometry):
  *                     the steps of a launch interleave, a few rows behind one another, so
  *                     the intermediate states stay in the L2 and HBM sees about one read and
  *                     two writes per launch instead of one read and one write per step.
- *                     LBM_ORDER_AUTO: the wavefront when both buffers of the lattices exceed
- *                     64 MB, else step order.
+ *                     LBM_ORDER_AUTO: step order (measured on GB300: the wavefront gains
+ *                     on single-model lattices of a few GB, loses on mixed-model groups
+ *                     and on 16384^2 lattices, where issue and latency, not HBM, bound it).
  * Applies to the context's next lbm_step and to groups created afterwards (a group takes the
  * shape of its first context).  Errors: LBM_ERR_INVALID_ARG for a negative step count or an
  * unknown order. */

@@ -58,9 +58,9 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_step_kernel(const S* __rest
     const unsigned stride = gridDim.x * blockDim.x;
     // constants precomputed on the host in both precisions (no FP64 set-up in the kernel)
     const T* ct = adj_consts<T>(a);
-    const T w = ct[0], w3 = ct[1], w4 = ct[2], rho0 = ct[3], urx = ct[4], ury = ct[5];
-    const T Px[3] = {ct[6], ct[7], ct[8]};
-    const T Py[3] = {ct[9], ct[10], ct[11]};
+    VjpConsts<T> vc;
+    vc.w = ct[0]; vc.w3 = ct[1]; vc.w4 = ct[2]; vc.rho0 = ct[3]; vc.urx = ct[4]; vc.ury = ct[5];
+    vc.Xr = ct[12]; vc.Yr = ct[13];
     // per-thread sums in the collision precision (a thread handles a few nodes), FP64 from
     // the block fold on
     T acc[3] = {T(0), T(0), T(0)};
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_step_kernel(const S* __rest
 #pragma unroll
             for (int i = 0; i < 9; ++i) { g[i] = f[i][j]; v[i] = l[i][j]; }
             T wb, w3b, w4b;
-            collide_vjp<MODEL, T>(g, v, gb, w, w3, w4, rho0, Px, Py, urx, ury, wb, w3b, w4b);
+            collide_vjp<MODEL, T>(g, v, gb, vc, wb, w3b, w4b);
 #pragma unroll
             for (int i = 0; i < 9; ++i) out[i][j] = gb[i];
             if (active && j < nvalid) {

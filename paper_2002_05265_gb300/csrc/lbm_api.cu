@@ -305,8 +305,7 @@ cudaError_t launch_tile(lbm_group* g, const void* const* buf0, void* const* buf1
     ta.witems = 0;
     const int order = g->ctx[0]->launch_order;
     unsigned long long items = (unsigned long long)nsteps * g->ttotal;
-    if (nsteps > 1 && g->same_geometry && order != LBM_ORDER_STEP &&
-        (order == LBM_ORDER_WAVE || g->state_bytes > (64ll << 20))) {
+    if (nsteps > 1 && g->same_geometry && order == LBM_ORDER_WAVE) {
         // skew: a dependency lies about two grid-widths of work items back
         const long long per_key = (long long)nsteps * (long long)ta.n * g->wntx;
         const int D = (int)std::max<long long>(4, (2LL * g->tgrid[sh] + per_key - 1) / per_key + 1);
@@ -394,8 +393,7 @@ int tile_steps_per_launch(const lbm_group* g) {
     int per;
     if (g->ctx[0]->launch_steps > 0) {
         per = g->ctx[0]->launch_steps;
-    } else if (g->same_geometry && g->ctx[0]->launch_order != LBM_ORDER_STEP &&
-               (g->ctx[0]->launch_order == LBM_ORDER_WAVE || g->state_bytes > (64ll << 20))) {
+    } else if (g->same_geometry && g->ctx[0]->launch_order == LBM_ORDER_WAVE) {
         per = 16;   // wavefront: the intermediate states stay in the L2
     } else {
         const int grid = std::max(1, std::max(g->tgrid[0], g->tgrid[1]));
@@ -868,6 +866,11 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
             g->tkernel[sh] = k;
             g->tgrid[sh] = sms * per_sm;   // all resident CTAs (a multi-step launch needs them co-resident)
         }
+        // the library's choice: a step with fewer tiles than resident CTAs leaves the copy
+        // pipeline mostly idle (latency-bound); the register-staged kernels do better there
+        bool forced = false;
+        for (int k = 0; k < n; ++k) forced = forced || ctxs[k]->path == LBM_PATH_BULK;
+        if (tile && !forced && off < (unsigned)std::max(g->tgrid[0], g->tgrid[1])) tile = false;
         if (!tile) {
             g->tbegin.clear();
             g->cbase.clear();
