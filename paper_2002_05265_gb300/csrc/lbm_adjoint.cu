@@ -43,19 +43,19 @@ template <typename T> __device__ __forceinline__ const T* adj_consts(const AdjAr
 template <> __device__ __forceinline__ const float* adj_consts<float>(const AdjArgs& a) { return a.cf; }
 template <> __device__ __forceinline__ const double* adj_consts<double>(const AdjArgs& a) { return a.cd; }
 
-// One adjoint step: lam_out = J^T (reverse-streamed lam_in) at every node; the rate
-// sensitivities are accumulated into this block's FP64 slot of `rate_part` (3 per block).
+// One adjoint step: lam_out = J^T (reverse-streamed lam_in) at every node, done by `nblk`
+// blocks of which this is block `blk`; the rate sensitivities are accumulated into this
+// block's FP64 slot of `rate_part` (3 per block).
 template <int MODEL, typename S>
-__global__ void __launch_bounds__(kAdjBlock) adjoint_step_kernel(const S* __restrict__ state,
-                                                                 const typename Conv<S>::T* __restrict__ lam_in,
-                                                                 typename Conv<S>::T* __restrict__ lam_out,
-                                                                 AdjArgs a, double* __restrict__ rate_part) {
+__device__ __forceinline__ void adjoint_body(const S* __restrict__ state, const typename Conv<S>::T* __restrict__ lam_in,
+                                             typename Conv<S>::T* __restrict__ lam_out, const AdjArgs& a,
+                                             double* __restrict__ rate_part, unsigned blk, unsigned nblk) {
     using T = typename Conv<S>::T;
     constexpr int VEC = AdjVec<S>::value;
     const int lane = threadIdx.x & 31;
     const int nseg = (a.nx + VEC - 1) / VEC;
     const unsigned total = (unsigned)a.ny * (unsigned)nseg;
-    const unsigned stride = gridDim.x * blockDim.x;
+    const unsigned stride = nblk * blockDim.x;
     // constants precomputed on the host in both precisions (no FP64 set-up in the kernel)
     const T* ct = adj_consts<T>(a);
     VjpConsts<T> vc;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_step_kernel(const S* __rest
     // per-thread sums in the collision precision (a thread handles a few nodes), FP64 from
     // the block fold on
     T acc[3] = {T(0), T(0), T(0)};
-    for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+    for (unsigned base = blk * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
         const unsigned s = base + lane;
         const bool active = s < total;
         const unsigned sc = active ? s : total - 1;
@@ -111,8 +111,42 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_step_kernel(const S* __rest
     if (threadIdx.x < 3) {
         double x = 0.0;
         for (int w2 = 0; w2 < kAdjBlock / 32; ++w2) x += sh[w2][threadIdx.x];
-        rate_part[blockIdx.x * 3 + threadIdx.x] += x;
+        rate_part[blk * 3 + threadIdx.x] += x;
     }
+}
+
+template <int MODEL, typename S>
+__global__ void __launch_bounds__(kAdjBlock) adjoint_step_kernel(const S* __restrict__ state,
+                                                                 const typename Conv<S>::T* __restrict__ lam_in,
+                                                                 typename Conv<S>::T* __restrict__ lam_out,
+                                                                 AdjArgs a, double* __restrict__ rate_part) {
+    adjoint_body<MODEL, S>(state, lam_in, lam_out, a, rate_part, blockIdx.x, gridDim.x);
+}
+
+// One adjoint step of one checkpoint segment and, in the same launch, one recomputed forward
+// step of the next segment (independent work: the next segment's states go to the other
+// ring of buffers).  Blocks [0, nadj) run the adjoint step, the others the forward step, so
+// the two latency-bound passes share the SMs instead of following one another.
+template <int MODEL, typename S, bool SHIFT>
+__global__ void __launch_bounds__(kAdjBlock) adjoint_fused_kernel(const S* __restrict__ state,
+                                                                  const typename Conv<S>::T* __restrict__ lam_in,
+                                                                  typename Conv<S>::T* __restrict__ lam_out,
+                                                                  AdjArgs a, double* __restrict__ rate_part,
+                                                                  unsigned nadj, const S* __restrict__ fsrc,
+                                                                  S* __restrict__ fdst, StepArgs sa) {
+    if (blockIdx.x < nadj) {
+        adjoint_body<MODEL, S>(state, lam_in, lam_out, a, rate_part, blockIdx.x, nadj);
+        return;
+    }
+    using T = typename Conv<S>::T;
+    constexpr int VEC = DefaultVec<S>::value;
+    const int lane = threadIdx.x & 31;
+    const unsigned total = (unsigned)sa.ny * (unsigned)sa.nseg;
+    const unsigned stride = (gridDim.x - nadj) * blockDim.x;
+    const Consts<T> c = make_consts<T>(sa);
+    Diag dg;
+    for (unsigned base = (blockIdx.x - nadj) * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride)
+        step_segment<MODEL, 4, S, VEC, false, SHIFT>(fsrc, fdst, sa, c, base + lane, total, lane, dg);
 }
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -199,6 +233,21 @@ __global__ void adjoint_init_kernel(const S* __restrict__ state0, AdjArgs a,
     }
 }
 
+template <typename S, bool SH>
+const void* adjoint_fused_for(int model) {
+    switch (model) {
+        case BGK: return (const void*)adjoint_fused_kernel<BGK, S, SH>;
+        case RM: return (const void*)adjoint_fused_kernel<RM, S, SH>;
+        case HM: return (const void*)adjoint_fused_kernel<HM, S, SH>;
+        case CM: return (const void*)adjoint_fused_kernel<CM, S, SH>;
+        case CHM: return (const void*)adjoint_fused_kernel<CHM, S, SH>;
+        case CUM: return (const void*)adjoint_fused_kernel<CUM, S, SH>;
+        case PR: return (const void*)adjoint_fused_kernel<PR, S, SH>;
+        case RR: return (const void*)adjoint_fused_kernel<RR, S, SH>;
+        default: return nullptr;
+    }
+}
+
 template <typename S>
 const void* adjoint_kernel_for(int model) {
     switch (model) {
@@ -248,7 +297,36 @@ int adjoint_plan(int storage, int model, int nx, int ny, int pitch, long long pl
     p->grid_fwd = (int)std::min<long long>(need_f, (long long)sms * std::max(per_sm, 1));
     if (p->grid_adj < 1) p->grid_adj = 1;
     if (p->grid_fwd < 1) p->grid_fwd = 1;
+    // fused adjoint + recompute launches: the resident blocks split about 2 : 1 (the adjoint
+    // step costs about twice the forward step); the adjoint part never exceeds grid_adj,
+    // which sizes the per-block rate partials
+    p->step_fused = storage == LBM_F64
+                        ? (shifted ? adjoint_fused_for<double, true>(model) : adjoint_fused_for<double, false>(model))
+                        : (shifted ? adjoint_fused_for<float, true>(model) : adjoint_fused_for<float, false>(model));
+    p->grid_fused = 0;
+    p->nadj_fused = 0;
+    if (p->step_fused &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, p->step_fused, kAdjBlock, 0) == cudaSuccess &&
+        per_sm >= 1) {
+        const long long R = (long long)sms * per_sm;
+        const long long nadj = std::min<long long>(std::max<long long>(1, (2 * R) / 3), p->grid_adj);
+        const long long nfwd = std::min<long long>(std::max<long long>(1, R - nadj), need_f);
+        p->nadj_fused = (int)nadj;
+        p->grid_fused = (int)(nadj + nfwd);
+    } else {
+        cudaGetLastError();
+    }
     return LBM_OK;
+}
+
+cudaError_t adjoint_launch_fused(const AdjointPlan& p, const void* state, const void* lam_in, void* lam_out,
+                                 double* rate_part, const StepArgs& sa, const void* fsrc, void* fdst, cudaStream_t s) {
+    AdjArgs a = p.a;
+    StepArgs f = sa;
+    unsigned nadj = (unsigned)p.nadj_fused;
+    void* args[] = {(void*)&state, (void*)&lam_in, (void*)&lam_out, (void*)&a, (void*)&rate_part,
+                    (void*)&nadj, (void*)&fsrc, (void*)&fdst, (void*)&f};
+    return cudaLaunchKernel(p.step_fused, dim3(p.grid_fused), dim3(p.block), args, 0, s);
 }
 
 cudaError_t adjoint_launch_fwd(const AdjointPlan& p, const StepArgs& sa, const void* src, void* dst, cudaStream_t s) {

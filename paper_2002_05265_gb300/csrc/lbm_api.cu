@@ -1020,7 +1020,6 @@ int lbm_adjoint_run(lbm_ctx* c, long long nsteps, int loss, const double* ux_tar
     float fwd_ms = 0.f, bwd_ms = 0.f;
 #define LBM_ADJ(call) do { if (e == cudaSuccess) e = (call); } while (0)
     LBM_ADJ(cudaMalloc(&ckpt, (size_t)nseg * bufb));
-    LBM_ADJ(cudaMalloc(&ring, (size_t)K * bufb));
     LBM_ADJ(cudaMalloc(&lam, 2 * lamb));
     LBM_ADJ(cudaMalloc(&rate_part, rp.size() * sizeof(double)));
     LBM_ADJ(cudaMalloc(&loss_part, lp.size() * sizeof(double)));
@@ -1047,6 +1046,12 @@ int lbm_adjoint_run(lbm_ctx* c, long long nsteps, int loss, const double* ux_tar
         if (rc != LBM_OK) break;
     }
     LBM_ADJ(cudaEventRecord(ev[1], c->stream));
+    // the recomputation takes the forward run's kernel family (the context's own group); with
+    // the register-staged kernels each adjoint launch also recomputes a step of the next
+    // segment into a second ring (fused launches)
+    lbm_group* fg = (c->own_group && c->own_group->tiled) ? c->own_group : nullptr;
+    const bool fused = !fg && plan.grid_fused > 0 && nseg > 1 && K > 1;
+    LBM_ADJ(cudaMalloc(&ring, (size_t)(fused ? 2 : 1) * K * bufb));
     // seed lambda^N and the loss from f^N
     LBM_ADJ(lbm::adjoint_launch_seed(plan, c->buf[c->cur], loss, uxt, uyt, lam, loss_part, c->stream));
     LBM_ADJ(cudaMemsetAsync(rate_part, 0, rp.size() * sizeof(double), c->stream));
@@ -1054,10 +1059,9 @@ int lbm_adjoint_run(lbm_ctx* c, long long nsteps, int loss, const double* ux_tar
     // segment's states into the ring, run its adjoint steps backwards.  A full segment is one
     // CUDA-graph replay (one graph per starting parity of the lambda ping-pong).
     cudaGraphExec_t seg_exec[2] = {nullptr, nullptr};
+    cudaGraphExec_t pair_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     cudaStream_t cap = nullptr;
     LBM_ADJ(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    // the recomputation takes the forward run's kernel family (the context's own group)
-    lbm_group* fg = (c->own_group && c->own_group->tiled) ? c->own_group : nullptr;
     auto enqueue_segment = [&](long long len, int parity, cudaStream_t st) {
         cudaError_t r = cudaSuccess;
         if (fg && len > 1) {   // the whole recomputation in one multi-step launch along the ring
@@ -1075,7 +1079,65 @@ int lbm_adjoint_run(lbm_ctx* c, long long nsteps, int loss, const double* ux_tar
         }
         return r;
     };
-    for (long long s2 = nseg - 1; s2 >= 0 && e == cudaSuccess && rc == LBM_OK; --s2) {
+    // fused: the adjoint steps of the segment in ring `slot` (len states) together with the
+    // recomputation of the next segment (lenn states) into ring `slot ^ 1`
+    char* rings[2] = {ring, fused ? ring + (size_t)K * bufb : ring};
+    auto enqueue_pair = [&](long long len, long long lenn, int slot, int parity, cudaStream_t st) {
+        cudaError_t r = cudaSuccess;
+        int pl = parity;
+        const long long nl = std::max(len, lenn - 1);
+        for (long long j = 0; j < nl && r == cudaSuccess; ++j) {
+            const bool adj = j < len, fw = j + 1 < lenn;
+            const long long k = len - 1 - j;
+            char* nx = rings[slot ^ 1];
+            if (adj && fw)
+                r = lbm::adjoint_launch_fused(plan, rings[slot] + k * bufb, lam + pl * lamb, lam + (pl ^ 1) * lamb,
+                                              rate_part, sa, nx + j * bufb, nx + (j + 1) * bufb, st);
+            else if (adj)
+                r = lbm::adjoint_launch_step(plan, rings[slot] + k * bufb, lam + pl * lamb, lam + (pl ^ 1) * lamb,
+                                             rate_part, st);
+            else
+                r = lbm::adjoint_launch_fwd(plan, sa, nx + j * bufb, nx + (j + 1) * bufb, st);
+            if (adj) pl ^= 1;
+        }
+        return r;
+    };
+    if (fused) {
+        // the first segment processed (the last in time) is recomputed on its own
+        const long long s0 = nseg - 1, len0 = std::min(K, N - s0 * K);
+        LBM_ADJ(cudaMemcpyAsync(rings[0], ckpt + s0 * bufb, bufb, cudaMemcpyDeviceToDevice, c->stream));
+        for (long long k = 0; k + 1 < len0 && e == cudaSuccess; ++k)
+            LBM_ADJ(lbm::adjoint_launch_fwd(plan, sa, rings[0] + k * bufb, rings[0] + (k + 1) * bufb, c->stream));
+    }
+    for (long long q = 0; fused && q < nseg && e == cudaSuccess && rc == LBM_OK; ++q) {
+        const long long s2 = nseg - 1 - q;
+        const long long len = std::min(K, N - s2 * K);
+        const long long lenn = (q + 1 < nseg) ? K : 0;   // every segment before the last is full
+        const int slot = (int)(q & 1);
+        if (lenn > 0)
+            LBM_ADJ(cudaMemcpyAsync(rings[slot ^ 1], ckpt + (s2 - 1) * bufb, bufb, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        if (len == K && lenn == K) {
+            cudaGraphExec_t& ex = pair_exec[slot][cur_l];
+            if (!ex && e == cudaSuccess) {
+                cudaGraph_t graph = nullptr;
+                LBM_ADJ(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+                const cudaError_t r = enqueue_pair(len, lenn, slot, cur_l, cap);
+                const cudaError_t r2 = cudaStreamEndCapture(cap, &graph);
+                LBM_ADJ(r);
+                LBM_ADJ(r2);
+                if (graph) {
+                    LBM_ADJ(cudaGraphInstantiate(&ex, graph, 0));
+                    cudaGraphDestroy(graph);
+                }
+            }
+            LBM_ADJ(cudaGraphLaunch(ex, c->stream));
+        } else {
+            LBM_ADJ(enqueue_pair(len, lenn, slot, cur_l, c->stream));
+        }
+        if (len % 2) cur_l ^= 1;
+    }
+    for (long long s2 = nseg - 1; !fused && s2 >= 0 && e == cudaSuccess && rc == LBM_OK; --s2) {
         const long long len = std::min(K, N - s2 * K);
         LBM_ADJ(cudaMemcpyAsync(ring, ckpt + s2 * bufb, bufb, cudaMemcpyDeviceToDevice, c->stream));
         if (len == K && K > 1) {
@@ -1097,8 +1159,11 @@ int lbm_adjoint_run(lbm_ctx* c, long long nsteps, int loss, const double* ux_tar
         }
         if (len % 2) cur_l ^= 1;
     }
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
         if (seg_exec[k]) cudaGraphExecDestroy(seg_exec[k]);
+        for (int j = 0; j < 2; ++j)
+            if (pair_exec[k][j]) cudaGraphExecDestroy(pair_exec[k][j]);
+    }
     if (cap) cudaStreamDestroy(cap);
     // dL/du0 from lambda^0 and the initial state (checkpoint 0)
     LBM_ADJ(lbm::adjoint_launch_init(plan, ckpt, lam + cur_l * lamb, gux, guy, c->stream));

@@ -80,12 +80,17 @@ struct AdjointPlan {
     const void* step_fwd;   // forward step kernel (src, dst, StepArgs), default shift
     const void* step_adj;   // adjoint step kernel of the model
     int grid_fwd, grid_adj, block;
+    const void* step_fused; // adjoint step + next segment's forward step in one launch
+    int grid_fused, nadj_fused;   // its grid and adjoint blocks (0: not available)
 };
 int adjoint_plan(int storage, int model, int nx, int ny, int pitch, long long plane, double w, double w3, double w4,
                  double rho0, double urx, double ury, AdjointPlan* p);
 cudaError_t adjoint_launch_fwd(const AdjointPlan& p, const StepArgs& sa, const void* src, void* dst, cudaStream_t s);
 cudaError_t adjoint_launch_step(const AdjointPlan& p, const void* state, const void* lam_in, void* lam_out,
                                 double* rate_part, cudaStream_t s);
+// One adjoint step (state, lam_in -> lam_out) and one forward step (fsrc -> fdst) in one launch.
+cudaError_t adjoint_launch_fused(const AdjointPlan& p, const void* state, const void* lam_in, void* lam_out,
+                                 double* rate_part, const StepArgs& sa, const void* fsrc, void* fdst, cudaStream_t s);
 int adjoint_seed_blocks();
 cudaError_t adjoint_launch_seed(const AdjointPlan& p, const void* state, int loss, const double* uxt,
                                 const double* uyt, void* lam, double* loss_part, cudaStream_t s);
