@@ -33,6 +33,7 @@ CHECK_EVERY = 100
 GRAPH_STEPS = 100
 NU = 1e-5
 MA = 0.1
+CS = 1.0 / np.sqrt(3.0)
 BYTES_PER_LU = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
 
 
@@ -62,6 +63,11 @@ def parse():
     p.add_argument("--sweep", default=None,
                    help="instead of the benchmark step, time single lattices: MODELS:STORAGES:SIZE, e.g. "
                         "all:f32,f16,bf16:16384 (one JSON line per combination)")
+    p.add_argument("--stability-map", type=int, default=0,
+                   help="instead of the benchmark step, the numerical stability maps of the convected vortex "
+                        "on an LxL lattice (L given): maximal stable Mach number per model, rate preset and viscosity")
+    p.add_argument("--map-tc", type=float, default=50.0, help="characteristic times t_c = L/u0 per map instance")
+    p.add_argument("--map-storage", default="f32", choices=["f64", "f32"])
     p.add_argument("--path", default="auto", choices=["auto", "vector", "bulk"],
                    help="step-kernel family: copy-engine staged (bulk), register-staged (vector), or the "
                         "library's choice (auto: bulk where the row length allows it)")
@@ -316,6 +322,72 @@ def run_reference(args, rank, world):
     print(json.dumps(out))
 
 
+MAP_CONFIGS = [("bgk", "srt")] + [(m, c) for m in ("rm", "hm", "cm", "chm", "k", "rr") for c in ("srt", "reg")]
+
+
+def run_stability_map(args):
+    """Numerical stability maps of the convected vortex (Sec. 5b): for every collision model in
+    both rate presets (SRT: omega_3 = omega_4 = omega_nu; REG: omega_3 = omega_4 = 1), every
+    viscosity nu in 1e-6 .. 1e-1 (half decades) and Mach number Ma in 0.05 .. 0.8, an LxL
+    vortex (beta = 0.5, R = L/20, centred) is advanced for M t_c = M L / u0 steps in the batched
+    persistent launch; an instance is unstable when its mean kinetic energy <|u|^2> exceeds
+    its initial value by more than 1% at a check (every 100 steps; the kinetic energy of this
+    flow only decays, an instability grows it exponentially), or rho / u turn non-finite.  Prints one
+    JSON line per (model, preset, nu) with the stable Mach numbers and the largest Ma below
+    which every tested Ma is stable (the stability curve of the paper's figures)."""
+    import torch
+    from paper_2002_05265_gb300 import build, flows, lbm
+    build.build_library()
+    lbm.load_library()
+    n = args.stability_map
+    nus = [float(v) for v in np.logspace(-6, -1, 11)]
+    mas = [round(0.05 * k, 2) for k in range(1, 17)]
+    stream = torch.cuda.Stream()
+    stable = {}   # (model, preset, nu) -> {Ma: bool}
+    t_all, lu_all = 0.0, 0.0
+    for Ma in mas:
+        u0 = Ma * CS
+        steps = int(np.ceil(args.map_tc * n / u0 / CHECK_EVERY)) * CHECK_EVERY
+        rho, ux, uy = flows.vortex(n, Ma=Ma, radius_frac=0.05)
+        ke0 = float(np.mean(ux * ux + uy * uy))
+        descs = []
+        for m, preset in MAP_CONFIGS:
+            for nu in nus:
+                w = 1.0 / (3.0 * nu + 0.5)
+                rates = (w, w, w) if preset == "srt" else (w, 1.0, 1.0)
+                descs.append({"nx": n, "ny": n, "model": m, "rates": rates, "ux_ref": u0, "uy_ref": 0.0,
+                              "ke_ref": ke0, "ke_factor": 1.01})
+        b = lbm.lbm_batch_create(descs, storage=args.map_storage, stream=stream)
+        cat = [torch.from_numpy(np.ascontiguousarray(np.tile(a.ravel(), len(descs)))).cuda() for a in (rho, ux, uy)]
+        lbm.lbm_batch_init_equilibrium(b, *cat)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            lbm.lbm_batch_run(b, steps, check_every=CHECK_EVERY, growth=1e300)
+            e1.record(stream)
+            stream.synchronize()
+        t_all += e0.elapsed_time(e1) / 1e3
+        st, bs, done, _ = lbm.lbm_batch_status(b, len(descs))
+        lu_all += float(sum(int(x) for x in done)) * n * n
+        lbm.lbm_batch_destroy(b)
+        k = 0
+        for m, preset in MAP_CONFIGS:
+            for nu in nus:
+                stable.setdefault((m, preset, nu), {})[Ma] = bool(st[k] == 0)
+                k += 1
+    for (m, preset, nu), res in stable.items():
+        ma_max = 0.0
+        for Ma in mas:
+            if not res[Ma]:
+                break
+            ma_max = Ma
+        print(json.dumps({"stability_map": True, "lattice": f"{n}x{n}", "tc": args.map_tc, "model": m,
+                          "preset": preset, "nu": nu, "ma_max": ma_max,
+                          "stable_ma": [Ma for Ma in mas if res[Ma]], "storage": args.map_storage}), flush=True)
+    print(json.dumps({"stability_map_summary": True, "lattice": f"{n}x{n}", "instances": len(stable) * len(mas),
+                      "lattice_updates": lu_all, "seconds": t_all, "glups": lu_all / t_all / 1e9}), flush=True)
+
+
 def run_accuracy(args):
     """Error of reduced-precision storage after 10 domain traversals of the convected vortex
     (Ma = 0.2, radius 0.1 L, L x L, no seed noise, so that nothing but the storage differs):
@@ -509,6 +581,9 @@ def main():
         return
     if args.accuracy:
         run_accuracy(args)
+        return
+    if args.stability_map:
+        run_stability_map(args)
         return
     import torch
     from paper_2002_05265_gb300 import build, flows, lbm
