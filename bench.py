@@ -67,6 +67,9 @@ def parse():
                    help="instead of the benchmark step, the numerical stability maps of the convected vortex "
                         "on an LxL lattice (L given): maximal stable Mach number per model, rate preset and viscosity")
     p.add_argument("--map-tc", type=float, default=50.0, help="characteristic times t_c = L/u0 per map instance")
+    p.add_argument("--lsa", type=int, default=0,
+                   help="instead of the benchmark step, linear stability curves (App. A) on a KxK wavenumber grid "
+                        "(K given): largest linearly stable Ma per model, rate preset and viscosity")
     p.add_argument("--map-storage", default="f32", choices=["f64", "f32"])
     p.add_argument("--path", default="auto", choices=["auto", "vector", "bulk"],
                    help="step-kernel family: copy-engine staged (bulk), register-staged (vector), or the "
@@ -388,6 +391,54 @@ def run_stability_map(args):
                       "lattice_updates": lu_all, "seconds": t_all, "glups": lu_all / t_all / 1e9}), flush=True)
 
 
+def run_lsa_map(args):
+    """Linear stability curves of the stream-and-collide scheme (Sec. 4c, App. A): for every
+    model in both rate presets and nu in 1e-6 .. 1e-1, the largest Mach number (bisection to
+    1e-3) for which no plane wave grows, max over a K x K wavenumber grid on [-pi, pi]^2 and 16
+    mean-flow angles phi in [0, pi/4] (the D2Q9 symmetries cover the rest) of
+    Im(omega) <= 1e-10 (the conserved modes at k = 0 have exactly 0).  Uses lbm_lsa_growth (the
+    exact Jacobian of this library's collision, FP64 eigenvalues on the GPU)."""
+    import torch
+    from paper_2002_05265_gb300 import build, lbm
+    build.build_library()
+    lbm.load_library()
+    K = args.lsa
+    k1 = np.linspace(-np.pi, np.pi, K)
+    ks = torch.from_numpy(np.array([(a, b) for a in k1 for b in k1])).cuda()
+    phis = np.linspace(0.0, np.pi / 4.0, 16)
+    nus = [float(v) for v in np.logspace(-6, -1, 11)]
+    growth = torch.empty((len(phis), K * K), dtype=torch.float64, device="cuda")
+    calls, t0 = 0, time.perf_counter()
+
+    def unstable(m, rates, ma):
+        u = ma * CS
+        fl = torch.from_numpy(np.stack([np.ones_like(phis), u * np.cos(phis), u * np.sin(phis)], axis=1)).cuda()
+        lbm.lbm_lsa_growth(m, rates, fl, ks, growth)
+        return float(growth.max()) > 1e-10
+
+    for m, preset in MAP_CONFIGS:
+        for nu in nus:
+            w = 1.0 / (3.0 * nu + 0.5)
+            rates = (w, w, w) if preset == "srt" else (w, 1.0, 1.0)
+            if unstable(m, rates, 0.0):
+                ma_max = 0.0
+            else:
+                lo, hi = 0.0, 1.0
+                while hi - lo > 1e-3:
+                    mid = 0.5 * (lo + hi)
+                    if unstable(m, rates, mid):
+                        hi = mid
+                    else:
+                        lo = mid
+                    calls += 1
+                ma_max = lo
+            calls += 1
+            print(json.dumps({"lsa": True, "model": m, "preset": preset, "nu": nu, "ma_max": round(ma_max, 4),
+                              "k_grid": K, "angles": len(phis)}), flush=True)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"lsa_summary": True, "calls": calls, "matrices": calls * len(phis) * K * K, "seconds": dt}))
+
+
 def run_accuracy(args):
     """Error of reduced-precision storage after 10 domain traversals of the convected vortex
     (Ma = 0.2, radius 0.1 L, L x L, no seed noise, so that nothing but the storage differs):
@@ -584,6 +635,9 @@ def main():
         return
     if args.stability_map:
         run_stability_map(args)
+        return
+    if args.lsa:
+        run_lsa_map(args)
         return
     import torch
     from paper_2002_05265_gb300 import build, flows, lbm

@@ -310,6 +310,26 @@ int lbm_batch_autotune(lbm_batch* b, long long trial_steps, int check_every, int
                        double* best_ms);
 const char* lbm_batch_last_error(const lbm_batch* b);
 
+/* ---- Linear stability analysis (App. A) ---------------------------------------------
+ * Growth rates of plane-wave perturbations of a uniform equilibrium state under the
+ * stream-and-collide iteration: f'(x + xi_i, t + 1) = G f'(x, t), G = d f* / d f the Jacobian
+ * of the collision map of `model` with `rates` at f = f^eq(rho, u) (Eq. extendedFeq), and for
+ * a wavenumber k the eigenproblem E^D(k) G A = exp(-i omega) A, E^D = diag(exp(-i xi_i . k))
+ * (Eq. EigenvaluePbDiscrete).  G is the exact derivative of this library's own collision;
+ * the eigenvalues come from a Hessenberg / shifted-QR solver in FP64 on the GPU.
+ *   flows   device, nflows x 3 doubles (rho, ux, uy) of the base states
+ *   k       device, nk x 2 doubles (kx, ky), radians per lattice spacing
+ *   growth  device, nflows x nk doubles (row-major by flow): max over the nine modes of
+ *           Im(omega) = ln |exp(-i omega)|
+ *   eig     optional device, nflows x nk x 9 complex eigenvalues (re, im pairs)
+ *   jac     optional device, nflows x 81 doubles: G row-major (G[i][j] = d f*_i / d f_j)
+ * Synchronous on `stream`.  Errors: LBM_ERR_INVALID_ARG for an unknown model, a rate outside
+ * (0, 2), a host pointer or more than 2^31 flow x wavenumber pairs; LBM_ERR_TIMEOUT if the QR
+ * iteration did not converge for some matrix (its growth entry is NaN); LBM_ERR_CUDA /
+ * LBM_ERR_NOMEM.  PR uses omega3 = omega4 = 1 whatever `rates` says. */
+int lbm_lsa_growth(int model, lbm_rates rates, const double* flows, int nflows, const double* k, int nk,
+                   double* growth, double* eig, double* jac, void* stream);
+
 /* Text of the last error on this context (never NULL); lbm_error_string names a code. */
 const char* lbm_last_error(const lbm_ctx* ctx);
 const char* lbm_error_string(int code);

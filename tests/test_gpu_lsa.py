@@ -1,0 +1,104 @@
+"""GPU linear stability analysis (App. A) against the FP64 oracle: the collision-map Jacobian
+G = d f* / d f (the library's reverse mode vs the oracle's complex step through the paper's
+population-space collision) and the eigenvalues of E^D(k) G (per-thread Hessenberg / QR vs
+numpy's eigvals), on seeded base flows and wavenumbers."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import oracle.lbm as olbm  # noqa: E402
+import oracle.lsa as olsa  # noqa: E402
+
+MODELS = ["bgk", "rm", "hm", "cm", "chm", "k", "pr", "rr"]
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2002_05265_gb300 import build, lbm
+    build.build_library()
+    lbm.load_library()
+    return lbm
+
+
+def _flows(n, seed):
+    g = np.random.default_rng(seed)
+    ma = g.uniform(0.0, 0.6, n)
+    phi = g.uniform(0.0, 2.0 * np.pi, n)
+    u = ma / np.sqrt(3.0)
+    return np.stack([g.uniform(0.9, 1.1, n), u * np.cos(phi), u * np.sin(phi)], axis=1)
+
+
+def _gpu(L, model, rates, flows, ks):
+    fl = torch.from_numpy(np.ascontiguousarray(flows)).cuda()
+    kk = torch.from_numpy(np.ascontiguousarray(ks)).cuda()
+    growth = torch.empty((len(flows), len(ks)), dtype=torch.float64, device="cuda")
+    eig = torch.empty((len(flows), len(ks), 9, 2), dtype=torch.float64, device="cuda")
+    jac = torch.empty((len(flows), 9, 9), dtype=torch.float64, device="cuda")
+    L.lbm_lsa_growth(model, rates, fl, kk, growth, eig, jac)
+    e = eig.cpu().numpy()
+    return growth.cpu().numpy(), e[..., 0] + 1j * e[..., 1], jac.cpu().numpy()
+
+
+@pytest.mark.parametrize("preset", ["srt", "reg"])
+@pytest.mark.parametrize("model", MODELS)
+def test_jacobian_and_growth_match_oracle(L, model, preset):
+    """Six base flows (rho in [0.9, 1.1], Ma up to 0.6 in any direction, nu = 1e-3), twelve
+    wavenumbers: G within 1e-12, every eigenvalue within 1e-10, growth rates within 1e-10."""
+    rates = olbm.rates_from_nu(1e-3, preset)
+    flows = _flows(6, seed=2 * MODELS.index(model) + (preset == "reg"))
+    g = np.random.default_rng(5)
+    ks = g.uniform(-np.pi, np.pi, (12, 2))
+    growth, eig, jac = _gpu(L, model, rates, flows, ks)
+    for f, (rho, ux, uy) in enumerate(flows):
+        G = olsa.collision_map_jacobian(model, rho, ux, uy, rates)
+        assert np.max(np.abs(jac[f] - G)) <= 1e-12
+        for k, (kx, ky) in enumerate(ks):
+            lam = olsa.eigenvalues(G, kx, ky)
+            # multiset match: each oracle eigenvalue has a GPU eigenvalue within 1e-10
+            d = np.abs(lam[:, None] - eig[f, k][None, :])
+            assert np.max(np.min(d, axis=1)) <= 1e-10
+            assert abs(growth[f, k] - np.max(np.log(np.abs(lam)))) <= 1e-10
+
+
+@pytest.mark.parametrize("model", ["bgk", "rm", "hm", "cm", "chm", "rr"])
+def test_flow_at_rest_is_linearly_stable(L, model):
+    """Sec. 4b: at Ma = 0 and nu = 1e-6 these models (SRT) have no growing mode on a 33 x 33
+    wavenumber grid over [-pi, pi]^2 (the conserved modes at k = 0 have growth exactly 0)."""
+    rates = olbm.rates_from_nu(1e-6, "srt")
+    k1 = np.linspace(-np.pi, np.pi, 33)
+    ks = np.array([(a, b) for a in k1 for b in k1])
+    growth, _, _ = _gpu(L, model, rates, np.array([[1.0, 0.0, 0.0]]), ks)
+    assert np.max(growth) <= 1e-12
+
+
+def test_srt_moment_models_share_the_bgk_spectrum(L):
+    """App. B: with omega_3 = omega_4 = omega_nu, RM, HM, CM and CHM are the BGK collision, so
+    their spectra coincide with BGK's for a moving base flow."""
+    rates = olbm.rates_from_nu(1e-4, "srt")
+    flows = _flows(4, seed=9)
+    ks = np.random.default_rng(3).uniform(-np.pi, np.pi, (16, 2))
+    ref, _, jref = _gpu(L, "bgk", rates, flows, ks)
+    for m in ("rm", "hm", "cm", "chm"):
+        g, _, j = _gpu(L, m, rates, flows, ks)
+        assert np.max(np.abs(j - jref)) <= 1e-12
+        assert np.max(np.abs(g - ref)) <= 1e-10
+
+
+def test_lsa_argument_checks(L):
+    flows = np.array([[1.0, 0.0, 0.0]])
+    ks = np.zeros((1, 2))
+    out = torch.empty((1, 1), dtype=torch.float64, device="cuda")
+    fl = torch.from_numpy(flows).cuda()
+    kk = torch.from_numpy(ks).cuda()
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_lsa_growth("bgk", (2.5, 1.0, 1.0), fl, kk, out)
+    assert e.value.code == L.LBM_ERR_INVALID_ARG
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_lsa_growth("bgk", (1.5, 1.0, 1.0), flows, kk, out)   # host flows
+    assert e.value.code == L.LBM_ERR_INVALID_ARG
