@@ -67,6 +67,9 @@ def parse():
                    help="instead of the benchmark step, the numerical stability maps of the convected vortex "
                         "on an LxL lattice (L given): maximal stable Mach number per model, rate preset and viscosity")
     p.add_argument("--map-tc", type=float, default=50.0, help="characteristic times t_c = L/u0 per map instance")
+    p.add_argument("--transport", type=int, default=0,
+                   help="instead of the benchmark step, the long-distance vortex transport of Sec. 5c on an LxL "
+                        "lattice (L given): Ma = 0.5, nu = 1e-4, 50 t_c, SRT-RR / REG-CHM / REG-K vorticity errors")
     p.add_argument("--lsa", type=int, default=0,
                    help="instead of the benchmark step, linear stability curves (App. A) on a KxK wavenumber grid "
                         "(K given): largest linearly stable Ma per model, rate preset and viscosity")
@@ -391,6 +394,72 @@ def run_stability_map(args):
                       "lattice_updates": lu_all, "seconds": t_all, "glups": lu_all / t_all / 1e9}), flush=True)
 
 
+def vorticity(ux, uy):
+    """omega_z = d uy/dx - d ux/dy by periodic central differences (arrays [y][x])."""
+    return 0.5 * ((np.roll(uy, -1, 1) - np.roll(uy, 1, 1)) - (np.roll(ux, -1, 0) - np.roll(ux, 1, 0)))
+
+
+def run_transport(args):
+    """Vortex transport over long distances (Sec. 5c): Ma = 0.5, nu = 1e-4, beta = 0.5,
+    R = L/20, 50 t_c = 50 L / u0 steps (the exact solution is the initial vortex moved by 50 L,
+    i.e. back at its start), FP32, for the most stable models SRT-RR, REG-CHM and REG-K.
+    Reports per model: normalised L2 error of the vorticity against the initial field
+    (normalised by its max - min, as in the paper's figures), the peak-vorticity ratio
+    (dissipation), the shift of the vorticity-weighted centre from the start (dispersion),
+    and the difference between REG-CHM and SRT-RR."""
+    import torch
+    from paper_2002_05265_gb300 import build, flows, lbm
+    build.build_library()
+    lbm.load_library()
+    n = args.transport
+    Ma, nu = 0.5, 1e-4
+    u0 = Ma * CS
+    steps = int(round(50 * n / u0))
+    steps += steps % 2
+    rho, ux, uy = flows.vortex(n, Ma=Ma, radius_frac=0.05)
+    w0 = vorticity(ux, uy)
+    span = float(w0.max() - w0.min())
+    dev = [torch.from_numpy(a).cuda() for a in (rho, ux, uy)]
+    w = 1.0 / (3.0 * nu + 0.5)
+    y, x = np.meshgrid(np.arange(n, dtype=float), np.arange(n, dtype=float), indexing="ij")
+
+    def centre(om):
+        a = np.abs(om - np.median(om))
+        # circular mean of the position (periodic domain)
+        cx = np.angle(np.sum(a * np.exp(2j * np.pi * x / n))) * n / (2 * np.pi) % n
+        cy = np.angle(np.sum(a * np.exp(2j * np.pi * y / n))) * n / (2 * np.pi) % n
+        return cx, cy
+
+    c0 = centre(w0)
+    out = {}
+    for name, m, rates in (("SRT-RR", "rr", (w, w, w)), ("REG-CHM", "chm", (w, 1.0, 1.0)), ("REG-K", "k", (w, 1.0, 1.0))):
+        lat = lbm.Lattice(n, n, lbm.MODELS[m], rates, storage=lbm.LBM_F32)
+        lat.set_shift_velocity(u0, 0.0)
+        lat.init_equilibrium(*dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lat.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        st = lat.status()[0]
+        gx = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        gy = torch.empty_like(gx)
+        lat.moments(None, gx, gy)
+        lat.close()
+        om = vorticity(gx.cpu().numpy(), gy.cpu().numpy())
+        c = centre(om)
+        dx = (c[0] - c0[0] + n / 2) % n - n / 2
+        dy = (c[1] - c0[1] + n / 2) % n - n / 2
+        out[name] = om
+        print(json.dumps({"transport": True, "model": name, "lattice": f"{n}x{n}", "steps": steps, "status": st,
+                          "l2_vorticity_error": float(np.sqrt(np.mean((om - w0) ** 2)) / span),
+                          "peak_ratio": float((om.max() - om.min()) / span),
+                          "centre_shift": [float(dx), float(dy)], "ms": e0.elapsed_time(e1),
+                          "glups": n * n * steps / (e0.elapsed_time(e1) / 1e3) / 1e9}), flush=True)
+    d = float(np.sqrt(np.mean((out["REG-CHM"] - out["SRT-RR"]) ** 2)) / span)
+    print(json.dumps({"transport_summary": True, "lattice": f"{n}x{n}", "reg_chm_vs_srt_rr_l2": d}))
+
+
 def run_lsa_map(args):
     """Linear stability curves of the stream-and-collide scheme (Sec. 4c, App. A): for every
     model in both rate presets and nu in 1e-6 .. 1e-1, the largest Mach number (bisection to
@@ -638,6 +707,9 @@ def main():
         return
     if args.lsa:
         run_lsa_map(args)
+        return
+    if args.transport:
+        run_transport(args)
         return
     import torch
     from paper_2002_05265_gb300 import build, flows, lbm

@@ -83,7 +83,13 @@ __device__ int eig9(Cx (&a)[N][N], Cx (&lam)[N]) {
         }
         for (int r = c + 2; r < N; ++r) a[r][c] = cx(0.0);
     }
-    // shifted QR on the active block [lo, hi]
+    // shifted QR on the active block [lo, hi]; a subdiagonal entry is negligible against its
+    // two diagonal neighbours, or against the matrix norm when both are tiny (zero eigenvalues:
+    // with omega_3 = omega_4 = 1 the collision removes whole moments)
+    double anorm = 0.0;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) anorm += a[i][j].re * a[i][j].re + a[i][j].im * a[i][j].im;
+    anorm = sqrt(anorm);
     int hi = N - 1, sweeps = 0;
     while (hi >= 0) {
         if (hi == 0) {
@@ -94,7 +100,7 @@ __device__ int eig9(Cx (&a)[N][N], Cx (&lam)[N]) {
         int lo = hi;
         while (lo > 0) {
             const double sc = cabs(a[lo][lo]) + cabs(a[lo - 1][lo - 1]);
-            if (cabs(a[lo][lo - 1]) <= 1e-15 * (sc > 0.0 ? sc : 1.0)) {
+            if (cabs(a[lo][lo - 1]) <= 1e-15 * fmax(sc, 1e-3 * anorm)) {
                 a[lo][lo - 1] = cx(0.0);
                 break;
             }
@@ -112,7 +118,12 @@ __device__ int eig9(Cx (&a)[N][N], Cx (&lam)[N]) {
         const Cx disc = csqrt(0.25 * ((p - t) * (p - t)) + q * r);
         const Cx e1 = half_tr + disc, e2 = half_tr - disc;
         Cx mu = cabs(e1 - t) < cabs(e2 - t) ? e1 : e2;
-        if (sweeps % 11 == 10) mu = mu + cx(0.75 * cabs(a[hi][hi - 1]));   // exceptional shift
+        if (sweeps % 11 == 10) {   // exceptional shift, rotating in the complex plane
+            const double e = 0.75 * (cabs(a[hi][hi - 1]) + cabs(a[hi - 1][hi - 2 >= 0 ? hi - 2 : 0]));
+            double sn, cn;
+            sincos(0.7 * sweeps, &sn, &cn);
+            mu = a[hi][hi] + Cx{e * cn, e * sn};
+        }
         // QR step on a[lo..hi] - mu I with Givens rotations, then RQ + mu I
         Cx cs[N];
         double cc[N];

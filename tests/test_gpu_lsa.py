@@ -102,3 +102,19 @@ def test_lsa_argument_checks(L):
     with pytest.raises(L.LBMError) as e:
         L.lbm_lsa_growth("bgk", (1.5, 1.0, 1.0), flows, kk, out)   # host flows
     assert e.value.code == L.LBM_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("model", ["rm", "hm", "pr", "rr", "chm"])
+def test_qr_converges_with_equilibrated_high_orders(L, model):
+    """REG rates (omega_3 = omega_4 = 1) give the collision Jacobian zero eigenvalues; the QR
+    iteration still converges on a 64 x 64 wavenumber grid at nu = 3e-6 for mean flows up to
+    Ma = 0.7 in 16 directions, and the growth rates are finite."""
+    rates = olbm.rates_from_nu(3e-6, "reg")
+    k1 = np.linspace(-np.pi, np.pi, 64)
+    ks = np.array([(a, b) for a in k1 for b in k1])
+    phis = np.linspace(0.0, np.pi / 4.0, 16)
+    for ma in (0.003, 0.1, 0.4, 0.7):
+        u = ma / np.sqrt(3.0)
+        flows = np.stack([np.ones_like(phis), u * np.cos(phis), u * np.sin(phis)], axis=1)
+        growth, _, _ = _gpu(L, model, rates, flows, ks)
+        assert np.all(np.isfinite(growth))
