@@ -321,17 +321,20 @@ __device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], const Consts
         if (MODEL == CM) {
             d22 = w4 * k22;
         } else if (MODEL == CHM) {
-            // central Hermite: A~_22 = K~_22 - c_s^2 (K~_20 + K~_02)   (Eqs. CHpoly, CHMcoll)
-            d22 = w4 * (k22 - cs2 * (n20 + n02)) + cs2 * (d20 + d02);
+            // central Hermite: A~_22 = K~_22 - c_s^2 (K~_20 + K~_02) relaxed with w4, the
+            // second order with w (Eqs. CHpoly, CHMcoll): d22 = w4 A~_22 + c_s^2 (d20 + d02)
+            // = w4 k22 + c_s^2 (w - w4) (n20 + n02)
+            d22 = w4 * k22 + (cs2 * (w - w4)) * (n20 + n02);
         } else {
             // cumulants: C22 = K22 - (K20 K02 + 2 K11^2)/rho relaxes to 0 and K22* is rebuilt
             // with the post-collision second-order central moments (written for deviations
-            // from the equilibrium central moments rho c_s^2, 0, rho c_s^4)
-            const T c2 = T(1) - w;
-            const T K20 = c2 * n20, K02 = c2 * n02, K11 = c2 * n11;
-            const T C22 = k22 - cs2 * (n20 + n02) - (n20 * n02 + T(2) * n11 * n11) * irho;
-            const T K22 = (T(1) - w4) * C22 + cs2 * (K20 + K02) + (K20 * K02 + T(2) * K11 * K11) * irho;
-            d22 = k22 - K22;
+            // from the equilibrium central moments rho c_s^2, 0, rho c_s^4).  With S = n20 + n02,
+            // P = n20 n02 + 2 n11^2 and c = 1 - rate: C22 = k22 - c_s^2 S - P / rho,
+            // K22* = c4 C22 + c_s^2 c2 S + c2^2 P / rho, so
+            // d22 = k22 - K22* = w4 k22 + c_s^2 (c4 - c2) S + (c4 - c2^2) P / rho
+            const T c2 = T(1) - w, c4 = T(1) - w4;
+            const T P = n20 * n02 + T(2) * n11 * n11;
+            d22 = w4 * k22 + (cs2 * (c4 - c2)) * (n20 + n02) + ((c4 - c2 * c2) * P) * irho;
         }
         // back to raw moments: binomial shift by +u (linear, so it applies to d directly)
         D20 = d20; D02 = d02; D11 = d11;
