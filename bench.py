@@ -80,13 +80,13 @@ def parse():
     p.add_argument("--stages", type=int, default=0, help="shared-memory stages of the bulk-copy kernel (0 = default)")
     p.add_argument("--launch-steps", type=int, default=0,
                    help="time steps per bulk-copy launch (0 = the library's default)")
-    p.add_argument("--order", default="auto", choices=["auto", "step", "wave"],
+    p.add_argument("--order", default="auto", choices=["auto", "step", "wave", "block"],
                    help="work order of multi-step bulk-copy launches (auto: wavefront when the state exceeds 64 MB)")
     return p.parse_args()
 
 
 PATHS = {"auto": 0, "vector": 1, "bulk": 2}
-ORDERS = {"auto": 0, "step": 1, "wave": 2}
+ORDERS = {"auto": 0, "step": 1, "wave": 2, "block": 3}
 
 
 def shape_lattice(lat, args):

@@ -214,13 +214,15 @@ int lbm_set_kernel_path(lbm_ctx* ctx, int path, int stages);
  *                     the steps of a launch interleave, a few rows behind one another, so
  *                     the intermediate states stay in the L2 and HBM sees about one read and
  *                     two writes per launch instead of one read and one write per step.
+ *                     LBM_ORDER_BLOCK: step order with each CTA on a contiguous range of
+ *                     tiles (so mostly on one lattice, one collision model, per step).
  *                     LBM_ORDER_AUTO: step order (measured on GB300: the wavefront gains
  *                     on single-model lattices of a few GB, loses on mixed-model groups
  *                     and on 16384^2 lattices, where issue and latency, not HBM, bound it).
  * Applies to the context's next lbm_step and to groups created afterwards (a group takes the
  * shape of its first context).  Errors: LBM_ERR_INVALID_ARG for a negative step count or an
  * unknown order. */
-enum { LBM_ORDER_AUTO = 0, LBM_ORDER_STEP = 1, LBM_ORDER_WAVE = 2 };
+enum { LBM_ORDER_AUTO = 0, LBM_ORDER_STEP = 1, LBM_ORDER_WAVE = 2, LBM_ORDER_BLOCK = 3 };
 int lbm_set_launch_shape(lbm_ctx* ctx, int steps_per_launch, int order);
 
 /* Several contexts advanced together, one time step of each in turn (so a set of lattices

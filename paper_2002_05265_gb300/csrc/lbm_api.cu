@@ -298,8 +298,8 @@ cudaError_t launch_tile(lbm_group* g, const void* const* buf0, void* const* buf1
         e.ntx = e.rows > 1 ? 0 : (c->nx + W - 1) / W;
         e.begin = g->tbegin[k];
     }
-    // work order: wavefront for multi-step launches of one geometry when asked, or by default
-    // when the state does not fit in about half the L2 (then the interleaved steps reuse it)
+    // work order of a multi-step launch: step order (round-robin tiles, or contiguous tiles per
+    // CTA), or the wavefront for lattices of one geometry
     ta.wave = 0;
     ta.wU = ta.wntx = ta.wD = 0;
     ta.witems = 0;
@@ -319,14 +319,22 @@ cudaError_t launch_tile(lbm_group* g, const void* const* buf0, void* const* buf1
             items = w;
         }
     }
+    int grid = (int)std::min<unsigned long long>((unsigned long long)g->tgrid[sh], items);
+    if (nsteps > 1 && !ta.wave && order == LBM_ORDER_BLOCK) {
+        // contiguous tiles per CTA: every resident CTA, wD = ceil(total / grid) tiles per step
+        grid = g->tgrid[sh];
+        ta.wave = 2;
+        ta.wD = (int)((g->ttotal + (unsigned)grid - 1) / (unsigned)grid);
+        items = (unsigned long long)grid * (unsigned long long)ta.wD * (unsigned long long)nsteps;
+        ta.witems = (unsigned)std::min<unsigned long long>(items, 0xffffffffull);
+    }
     if (items >= (1ull << 32)) return cudaErrorInvalidValue;   // the caller splits longer runs
     cudaError_t e = cudaSuccess;
     if (nsteps > 1) e = cudaMemsetAsync(g->cnt, 0, sizeof(unsigned) * g->cunits, s);
     if (e != cudaSuccess) return e;
-    int grid = (int)std::min<unsigned long long>((unsigned long long)g->tgrid[sh], items);
     // wavefront items cycle fastest through segments, lattices and steps (power-of-two
     // extents in practice); an odd grid keeps a CTA from being pinned to one lattice or step
-    if (ta.wave && grid > 1 && (grid % 2) == 0) grid -= 1;
+    if (ta.wave == 1 && grid > 1 && (grid % 2) == 0) grid -= 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(lbm::kTileThreads);
@@ -787,7 +795,7 @@ int lbm_set_kernel_path(lbm_ctx* c, int path, int stages) {
 
 int lbm_set_launch_shape(lbm_ctx* c, int steps_per_launch, int order) {
     if (!c) return LBM_ERR_INVALID_ARG;
-    if (steps_per_launch < 0 || order < LBM_ORDER_AUTO || order > LBM_ORDER_WAVE)
+    if (steps_per_launch < 0 || order < LBM_ORDER_AUTO || order > LBM_ORDER_BLOCK)
         return set_err(c, LBM_ERR_INVALID_ARG, "invalid steps per launch or work order");
     c->launch_steps = steps_per_launch;
     c->launch_order = order;

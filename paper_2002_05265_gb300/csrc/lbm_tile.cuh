@@ -97,6 +97,9 @@ struct TileArgs {
     // geometry: wU units of wntx tiles each): wavefront, item ((k * nsteps + s) * n + e) * wntx
     // + x is segment x of unit u = (k - s * wD + s) mod wU of lattice e at step s, valid when
     // 0 <= k - s * wD < wU; witems items in all.
+    // wave = 2: step order with contiguous tiles per CTA: item i = c + gridDim.x * k is the
+    // k-th item of CTA c, tile c * wD + (k mod wD) of step k / wD (wD tiles per CTA and step),
+    // so a CTA keeps to one lattice (one collision model) within a step.
     int wave, wU, wntx, wD;
     unsigned witems;
     TileEntry e[kGroupMax];
@@ -224,6 +227,12 @@ __device__ __forceinline__ bool item_at(const TileArgs& g, unsigned i, int& step
         step = (int)(i / g.total);
         t = i - (unsigned)step * g.total;
         return true;
+    }
+    if (g.wave == 2) {
+        const unsigned c = i % gridDim.x, k = i / gridDim.x;
+        step = (int)(k / (unsigned)g.wD);
+        t = c * (unsigned)g.wD + (k - (unsigned)step * (unsigned)g.wD);
+        return t < g.total;
     }
     const unsigned x = i % (unsigned)g.wntx;
     i /= (unsigned)g.wntx;

@@ -17,7 +17,7 @@ LBM_BGK, LBM_RM, LBM_HM, LBM_CM, LBM_CHM, LBM_K, LBM_PR, LBM_RR = range(8)
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = range(4)
 LBM_PRESET_SRT, LBM_PRESET_REG = 0, 1
 LBM_PATH_AUTO, LBM_PATH_VECTOR, LBM_PATH_BULK = 0, 1, 2
-LBM_ORDER_AUTO, LBM_ORDER_STEP, LBM_ORDER_WAVE = 0, 1, 2
+LBM_ORDER_AUTO, LBM_ORDER_STEP, LBM_ORDER_WAVE, LBM_ORDER_BLOCK = 0, 1, 2, 3
 LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_CUDA, LBM_ERR_BLOWUP, LBM_ERR_TIMEOUT, LBM_ERR_NOMEM = \
     0, -1, -2, -3, -4, -5, -6
 
