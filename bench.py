@@ -257,7 +257,7 @@ def cpu_baseline():
     finally:
         pool.shutdown()
     lu = len(MODELS) * L * L
-    return {"value": lu / dt / 1e9, "unit": "GLUPS", "cores": procs, "kind": "oracle",
+    return {"value": lu / dt / 1e9, "unit": "GLUPS", "cores": procs, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"one time step of each of the {len(MODELS)} models on the {L}x{L} double shear layer "
                       f"({lu} lattice updates, {dt:.1f} s), numpy FP64, the models in {procs} parallel "
                       f"single-threaded processes"}
@@ -321,7 +321,7 @@ def run_reference(args, rank, world):
            "config": {"workload": f"double shear layer {L}x{L}, 8 models, one time step per model per step "
                                   f"(bounded sample of the {args.sim_steps}-step run)",
                       "lattice": f"{L}x{L}", "models": MODELS},
-           "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": procs, "kind": "oracle",
+           "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": procs, "host_cores": os.cpu_count(), "kind": "oracle",
                             "sample": "one time step of each of the 8 models per benchmark step, the models in "
                                       f"{procs} parallel single-threaded numpy processes"},
            "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
