@@ -334,3 +334,42 @@ def test_full_size_double_shear_layer_sampled(L, model):
         _, rx, ry = macroscopic(fr)
         assert abs(ux[y, x] - rx[P // 2, P // 2]) <= 1e-5
         assert abs(uy[y, x] - ry[P // 2, P // 2]) <= 1e-5
+
+
+def test_benchmark_group_configuration_sampled(L):
+    """The benchmark's own launch configuration: the eight 1024 x 1024 FP32 double-shear-layer
+    lattices (one per model, nu = 1e-5, BGK SRT and the others REG) in one group with 100-step
+    graph chunks, i.e. one copy-engine launch advancing all eight by 100 steps.  After those
+    100 steps, 2 sampled nodes per lattice (one at the periodic corner) agree with the oracle
+    run on the (2k + 3)^2 light-cone patch around each node within 1e-5 on u."""
+    N, k = 1024, 100
+    fields = flows.double_shear_layer(N, Ma=0.1)
+    dev = _dev(*fields)
+    lats = []
+    for m in MODELS:
+        rates = olbm.rates_from_nu(1e-5, "srt" if m == "bgk" else "reg")
+        lat = L.Lattice(N, N, L.MODELS[m], rates, storage=L.LBM_F32)
+        lat.init_equilibrium(*dev)
+        lats.append((m, rates, lat))
+    g = L.lbm_group_create([x[2].ctx for x in lats], graph_steps=100)
+    L.lbm_group_step(g, k)
+    P = 2 * k + 3
+    rng = np.random.default_rng(17)
+    for m, rates, lat in lats:
+        assert lat.status()[0] == L.LBM_OK
+        ux = torch.empty((N, N), dtype=torch.float64, device="cuda")
+        uy = torch.empty_like(ux)
+        lat.moments(None, ux, uy)
+        ux, uy = ux.cpu().numpy(), uy.cpu().numpy()
+        pts = [(int(rng.integers(0, N)), int(rng.integers(0, N))), (0, N - 1)]
+        for (y, x) in pts:
+            ys = (np.arange(P) + y - P // 2) % N
+            xs = (np.arange(P) + x - P // 2) % N
+            patch = [a[np.ix_(ys, xs)] for a in fields]
+            fr = olbm.run(olbm.init_equilibrium(*patch), m, rates, k)
+            _, rx, ry = macroscopic(fr)
+            assert abs(ux[y, x] - rx[P // 2, P // 2]) <= 1e-5, (m, y, x)
+            assert abs(uy[y, x] - ry[P // 2, P // 2]) <= 1e-5, (m, y, x)
+    L.lbm_group_destroy(g)
+    for _, _, lat in lats:
+        lat.close()
