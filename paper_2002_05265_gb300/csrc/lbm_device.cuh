@@ -310,22 +310,28 @@ __device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], const Consts
         D21 = n21 - c3 * a21; D12 = n12 - c3 * a12;
         D22 = (n22 - cs2 * (n20 + n02)) - c4 * a22 + cs2 * (D20 + D02);
     } else {
-        // central moments of f^neq: binomial shift by -u (first-order parts vanish)
-        const T k21 = n21 - T(2) * ux * n11 - uy * n20;
-        const T k12 = n12 - T(2) * uy * n11 - ux * n02;
-        const T k22 = n22 - T(2) * ux * n12 - T(2) * uy * n21 + uxx * n02 + uyy * n20 + T(4) * ux * uy * n11;
-        // removed central moments d = k - k*
-        const T d20 = w * n20, d02 = w * n02, d11 = w * n11;
-        const T d21 = w3 * k21, d12 = w3 * k12;
-        T d22;
-        if (MODEL == CM) {
-            d22 = w4 * k22;
-        } else if (MODEL == CHM) {
+        // central moments k = S(-u) n of f^neq (binomial shift, first-order parts vanish),
+        // relaxed by order (d = rates . k), shifted back D = S(u) d.  The three linear steps are
+        // folded into one expression in n: with a21 = 2 ux n11 + uy n20, a12 = 2 uy n11 + ux n02,
+        // R = 2 (ux n12 + uy n21) and Q = ux^2 n02 + uy^2 n20 + 4 ux uy n11 one has
+        // k21 = n21 - a21, k12 = n12 - a12, k22 = n22 - R + Q, and
+        //   D21 = w3 n21 + (w - w3) a21,   D12 = w3 n12 + (w - w3) a12,
+        //   D22 = w4 n22 + (w3 - w4) R + (w - 2 w3 + w4) Q + (model terms),
+        // the model terms being d22 - w4 k22 (zero for CM).
+        const T uxy = ux * uy;
+        const T a21 = T(2) * ux * n11 + uy * n20, a12 = T(2) * uy * n11 + ux * n02;
+        const T R = T(2) * (ux * n12 + uy * n21);
+        const T Q = uxx * n02 + uyy * n20 + T(4) * uxy * n11;
+        D20 = w * n20; D02 = w * n02; D11 = w * n11;
+        D21 = w3 * n21 + (w - w3) * a21;
+        D12 = w3 * n12 + (w - w3) * a12;
+        T D22c = w4 * n22 + (w3 - w4) * R + (w - T(2) * w3 + w4) * Q;
+        if (MODEL == CHM) {
             // central Hermite: A~_22 = K~_22 - c_s^2 (K~_20 + K~_02) relaxed with w4, the
             // second order with w (Eqs. CHpoly, CHMcoll): d22 = w4 A~_22 + c_s^2 (d20 + d02)
             // = w4 k22 + c_s^2 (w - w4) (n20 + n02)
-            d22 = w4 * k22 + (cs2 * (w - w4)) * (n20 + n02);
-        } else {
+            D22c += (cs2 * (w - w4)) * (n20 + n02);
+        } else if (MODEL != CM) {
             // cumulants: C22 = K22 - (K20 K02 + 2 K11^2)/rho relaxes to 0 and K22* is rebuilt
             // with the post-collision second-order central moments (written for deviations
             // from the equilibrium central moments rho c_s^2, 0, rho c_s^4).  With S = n20 + n02,
@@ -334,13 +340,9 @@ __device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], const Consts
             // d22 = k22 - K22* = w4 k22 + c_s^2 (c4 - c2) S + (c4 - c2^2) P / rho
             const T c2 = T(1) - w, c4 = T(1) - w4;
             const T P = n20 * n02 + T(2) * n11 * n11;
-            d22 = w4 * k22 + (cs2 * (c4 - c2)) * (n20 + n02) + ((c4 - c2 * c2) * P) * irho;
+            D22c += (cs2 * (c4 - c2)) * (n20 + n02) + ((c4 - c2 * c2) * P) * irho;
         }
-        // back to raw moments: binomial shift by +u (linear, so it applies to d directly)
-        D20 = d20; D02 = d02; D11 = d11;
-        D21 = d21 + T(2) * ux * d11 + uy * d20;
-        D12 = d12 + T(2) * uy * d11 + ux * d02;
-        D22 = d22 + T(2) * ux * d12 + T(2) * uy * d21 + uxx * d02 + uyy * d20 + T(4) * ux * uy * d11;
+        D22 = D22c;
     }
 
     // g* = g - (Eq. Q9postCollVDF_RM applied to D, with D_00 = D_10 = D_01 = 0)
