@@ -184,7 +184,8 @@ int lbm_status(lbm_ctx* ctx, int* status, long long* blowup_step, long long* ste
 int lbm_synchronize(lbm_ctx* ctx);
 
 /* Grid geometry actually used: row pitch in elements (>= nx, multiple of 32), CUDA grid and
- * block sizes of the step kernel. */
+ * block sizes of the context's register-staged step kernel (the copy-engine kernel of
+ * LBM_PATH_BULK / LBM_PATH_AUTO always runs 320-thread CTAs on every resident slot). */
 int lbm_get_layout(const lbm_ctx* ctx, int* pitch, int* grid, int* block);
 
 /* Kernel family that advances a context (library design choice; the paper has no
