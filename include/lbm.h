@@ -217,9 +217,10 @@ int lbm_set_kernel_path(lbm_ctx* ctx, int path, int stages);
  *                     two writes per launch instead of one read and one write per step.
  *                     LBM_ORDER_BLOCK: step order with each CTA on a contiguous range of
  *                     tiles (so mostly on one lattice, one collision model, per step).
- *                     LBM_ORDER_AUTO: step order (measured on GB300: the wavefront gains
- *                     on single-model lattices of a few GB, loses on mixed-model groups
- *                     and on 16384^2 lattices, where issue and latency, not HBM, bound it).
+ *                     LBM_ORDER_AUTO: the wavefront for a single lattice whose buffers exceed
+ *                     256 MB and that runs several steps per launch, else step order
+ *                     (measured on GB300: the wavefront gains on single-model lattices of a
+ *                     few GB, loses on mixed-model groups and with one-step launches).
  * Applies to the context's next lbm_step and to groups created afterwards (a group takes the
  * shape of its first context).  Errors: LBM_ERR_INVALID_ARG for a negative step count or an
  * unknown order. */

@@ -271,6 +271,17 @@ int launch_group_once(lbm_group* g, cudaStream_t s, int sh) {
     return LBM_OK;
 }
 
+// Wavefront order: when asked, and by default for a single lattice of a few hundred MB or
+// more that runs several steps per launch anyway (measured: 0.95-1.01 of HBM vs 0.92-0.95
+// in step order at 4096^2; mixed-model groups and one-step launches lose with it).
+bool use_wave(const lbm_group* g) {
+    const int order = g->ctx[0]->launch_order;
+    if (!g->same_geometry || order == LBM_ORDER_STEP || order == LBM_ORDER_BLOCK) return false;
+    if (order == LBM_ORDER_WAVE) return true;
+    const int grid = std::max(1, std::max(g->tgrid[0], g->tgrid[1]));
+    return g->ctx.size() == 1 && g->state_bytes > (256ll << 20) && g->ttotal < 64u * (unsigned)grid;
+}
+
 // bulk-copy staged launch of a tiled group: `nsteps` time steps of every context k, reading
 // buf0[k] at the first step (buffers buf0[k] and buf1[k] alternate; with nsteps = 1 they are
 // simply source and destination, as for the recomputation ring of the adjoint)
@@ -305,7 +316,7 @@ cudaError_t launch_tile(lbm_group* g, const void* const* buf0, void* const* buf1
     ta.witems = 0;
     const int order = g->ctx[0]->launch_order;
     unsigned long long items = (unsigned long long)nsteps * g->ttotal;
-    if (nsteps > 1 && g->same_geometry && order == LBM_ORDER_WAVE) {
+    if (nsteps > 1 && use_wave(g)) {
         // skew: a dependency lies about two grid-widths of work items back
         const long long per_key = (long long)nsteps * (long long)ta.n * g->wntx;
         const int D = (int)std::max<long long>(4, (2LL * g->tgrid[sh] + per_key - 1) / per_key + 1);
@@ -401,7 +412,7 @@ int tile_steps_per_launch(const lbm_group* g) {
     int per;
     if (g->ctx[0]->launch_steps > 0) {
         per = g->ctx[0]->launch_steps;
-    } else if (g->same_geometry && g->ctx[0]->launch_order == LBM_ORDER_WAVE) {
+    } else if (use_wave(g)) {
         per = 16;   // wavefront: the intermediate states stay in the L2
     } else {
         const int grid = std::max(1, std::max(g->tgrid[0], g->tgrid[1]));
