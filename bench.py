@@ -314,6 +314,20 @@ def run_reference(args, rank, world):
         pool.shutdown()
     lu = args.steps * len(MODELS) * L * L
     v = lu / dt / 1e9
+    # single-process figures beside it: one time step per model on the same lattice, and the
+    # 128 x 128 vortex (BGK, FP64, 1000 steps) run in full
+    import oracle.lbm as olbm
+    from paper_2002_05265_gb300 import flows
+    f0 = olbm.init_equilibrium(*flows.double_shear_layer(L, Ma=MA))
+    per_model = {}
+    for m in MODELS:
+        t0 = time.perf_counter()
+        olbm.step(f0, m, olbm.rates_from_nu(NU, _preset(m)))
+        per_model[m] = L * L / (time.perf_counter() - t0) / 1e6
+    vf = flows.vortex(128, Ma=0.1, noise=1e-8, seed=1)
+    t0 = time.perf_counter()
+    olbm.run(olbm.init_equilibrium(*vf), "bgk", olbm.rates_from_nu(1e-4, "srt"), 1000)
+    vortex_s = time.perf_counter() - t0
     out = {"impl": "reference", "metric": "D2Q9 lattice updates per second, 8 collision models",
            "value": v, "unit": "GLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -324,7 +338,8 @@ def run_reference(args, rank, world):
            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": procs, "host_cores": os.cpu_count(), "kind": "oracle",
                             "sample": "one time step of each of the 8 models per benchmark step, the models in "
                                       f"{procs} parallel single-threaded numpy processes"},
-           "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "single_process": {"per_model_mlups_1024": per_model, "vortex_128_bgk_1000_steps_seconds": vortex_s}}
     print(json.dumps(out))
 
 
