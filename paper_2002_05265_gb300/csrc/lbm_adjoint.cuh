@@ -38,7 +38,7 @@ __device__ __forceinline__ void collide_vjp(const T (&g)[9], const T (&v)[9], T 
     const T m20 = (a2p + a2z) + a2m, m02 = a0p + a0m, m11 = a1p - a1m;
     const T m21 = a2p - a2m, m12 = a1p + a1m, m22 = a2p + a2m;
     const T rho = c.rho0 + drho;
-    const T irho = T(1) / rho;
+    const T irho = recip(rho);
     const T ux = jx * irho, uy = jy * irho;
     const T uxx = ux * ux, uyy = uy * uy;
     const T X = uxx + cs2, Y = uyy + cs2;   // mu_2(u_x), mu_2(u_y)

@@ -160,8 +160,15 @@ __device__ __forceinline__ void vstore(S* p, const typename Conv<S>::T (&v)[VEC]
     *reinterpret_cast<R*>(p) = r;
 }
 
-// Correctly rounded reciprocal (the reciprocal intrinsic instead of a full division).
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// 1/x.  FP32: the hardware approximation (rcp.approx) refined by one Newton-Raphson step,
+// r' = r + r (1 - x r), two FMAs; within an ulp of the rounded quotient and free of any
+// data-dependent branch, so a lattice that has blown up (non-finite populations) steps as fast
+// as a healthy one.  FP64: the correctly rounded reciprocal intrinsic.
+__device__ __forceinline__ float recip(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
 __device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
 
 // Per-launch constants of the collision in the collision precision.
