@@ -28,6 +28,14 @@ namespace lbm {
 namespace {
 
 constexpr int kAdjBlock = 256;
+// Resident 256-thread blocks per SM the compiler must allow, which sets its register budget:
+// 2 (at most 128 registers a thread) for the FP32 and 16-bit kernels, whose register
+// allocation then runs the 512 x 512 adjoint 2-10 % faster than with the budget unstated
+// or capped at 80; unstated for FP64.
+#ifndef LBM_ADJ_MIN_BLOCKS
+#define LBM_ADJ_MIN_BLOCKS 2
+#endif
+template <typename S> constexpr int kAdjMinBlocks = sizeof(S) == 8 ? 0 : LBM_ADJ_MIN_BLOCKS;
 
 // Nodes per thread of the adjoint step: it holds the populations and the adjoints of every
 // node it handles, so it uses half the vector width of the forward kernel (FP32: 2 nodes,
@@ -116,7 +124,7 @@ __device__ __forceinline__ void adjoint_body(const S* __restrict__ state, const 
 }
 
 template <int MODEL, typename S>
-__global__ void __launch_bounds__(kAdjBlock) adjoint_step_kernel(const S* __restrict__ state,
+__global__ void __launch_bounds__(kAdjBlock, kAdjMinBlocks<S>) adjoint_step_kernel(const S* __restrict__ state,
                                                                  const typename Conv<S>::T* __restrict__ lam_in,
                                                                  typename Conv<S>::T* __restrict__ lam_out,
                                                                  AdjArgs a, double* __restrict__ rate_part) {
@@ -128,7 +136,7 @@ __global__ void __launch_bounds__(kAdjBlock) adjoint_step_kernel(const S* __rest
 // ring of buffers).  Blocks [0, nadj) run the adjoint step, the others the forward step, so
 // the two latency-bound passes share the SMs instead of following one another.
 template <int MODEL, typename S, bool SHIFT>
-__global__ void __launch_bounds__(kAdjBlock) adjoint_fused_kernel(const S* __restrict__ state,
+__global__ void __launch_bounds__(kAdjBlock, kAdjMinBlocks<S>) adjoint_fused_kernel(const S* __restrict__ state,
                                                                   const typename Conv<S>::T* __restrict__ lam_in,
                                                                   typename Conv<S>::T* __restrict__ lam_out,
                                                                   AdjArgs a, double* __restrict__ rate_part,
