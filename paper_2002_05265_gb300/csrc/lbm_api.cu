@@ -447,7 +447,8 @@ int launch_check(lbm_ctx* c, double* out8_dev, int apply) {
     CheckArgs ck;
     ck.ke_ref = c->ke_ref; ck.ke_factor = c->ke_factor; ck.uref_x = c->uref_x; ck.uref_y = c->uref_y;
     ck.step = c->steps; ck.apply = apply;
-    LBM_CK(c, lbm::launch_reduce(c->storage, c->buf[c->cur], field_args(c), c->partials, out8_dev,
+    unsigned* counter = reinterpret_cast<unsigned*>(c->partials + 8 * lbm::reduce_blocks());
+    LBM_CK(c, lbm::launch_reduce(c->storage, c->buf[c->cur], field_args(c), c->partials, counter, out8_dev,
                                  c->status, c->blowup_step, ck, c->stream));
     return LBM_OK;
 }
@@ -587,7 +588,8 @@ int lbm_create(lbm_ctx** out, int nx, int ny, int periodic, int model, lbm_rates
             e = cudaMemsetAsync(c->buf[b], 0, bytes, c->stream);
             if (e != cudaSuccess) break;
         }
-        if (e == cudaSuccess) e = cudaMalloc(&c->partials, sizeof(double) * 8 * lbm::reduce_blocks());
+        if (e == cudaSuccess) e = cudaMalloc(&c->partials, lbm::reduce_scratch_bytes());
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->partials, 0, lbm::reduce_scratch_bytes(), c->stream);
         if (e == cudaSuccess) e = cudaMalloc(&c->red_out, sizeof(double) * 8);
         if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int) + sizeof(long long) * 2);
         if (e == cudaSuccess) {

@@ -16,7 +16,9 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kReduceBlocks = 608;   // 4 x 152 SMs; fixed, so the fold order is deterministic
+constexpr int kReduceThreads = 128;  // threads of a reduction block (fewer threads, less FP64 folding)
 constexpr int kReduceValues = 8;
+constexpr int kReduceFlush = 2;      // row segments summed in the collision precision per FP64 add
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -103,9 +105,11 @@ __global__ void gather_kernel(const S* buf, FieldArgs a, double* f, double* rho,
     }
 }
 
-// Folds the per-thread accumulators of a block in a fixed order into its partial slot.
-__device__ __forceinline__ void block_fold_partials(double (&acc)[kReduceValues], double* partials) {
-    __shared__ double sh[kBlock / 32][kReduceValues];
+// Folds the per-thread values acc[0..7] of a block of kReduceThreads threads in a fixed order
+// (warp shuffles, then the warps in order; slot 6 by min, the others by sum); thread v < 8
+// returns the block's value v, the other threads return 0.
+__device__ __forceinline__ double block_fold(const double (&acc)[kReduceValues]) {
+    __shared__ double sh[kReduceThreads / 32][kReduceValues];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < kReduceValues; ++v) {
@@ -117,150 +121,43 @@ __device__ __forceinline__ void block_fold_partials(double (&acc)[kReduceValues]
         if (lane == 0) sh[warp][v] = x;
     }
     __syncthreads();
+    double x = 0.0;
     if (threadIdx.x < kReduceValues) {
         const int v = threadIdx.x;
-        double x = sh[0][v];
-        for (int w = 1; w < kBlock / 32; ++w) x = (v == 6) ? fmin(x, sh[w][v]) : x + sh[w][v];
-        partials[blockIdx.x * kReduceValues + v] = x;
+        x = sh[0][v];
+        for (int w = 1; w < kReduceThreads / 32; ++w) x = (v == 6) ? fmin(x, sh[w][v]) : x + sh[w][v];
     }
+    return x;
 }
 
-// Pass 1, per-node form: the same sums for layouts whose rows are not 16-byte aligned
-// (caller-owned buffers of lbm_reduce_noalloc may have any pitch); one node per thread,
-// scalar loads.
-template <typename S>
-__global__ void __launch_bounds__(kBlock) reduce_kernel_scalar(const S* buf, FieldArgs a, double* partials,
-                                                               double urefx, double urefy) {
-    using T = typename Conv<S>::T;
-    const long long n = (long long)a.nx * a.ny;
-    const T jx0 = T(a.rho0 * a.urx), jy0 = T(a.rho0 * a.ury);
+// Pass 2: folds nparts partials (fixed order: thread t takes parts t, t + 128, ..., then the
+// block fold), forms the outputs and applies the blow-up criterion.  Partials are read through
+// L2 (they may come from other blocks of the same launch).
+__device__ void finish_fold(const double* partials, int nparts, const FieldArgs& a, double* out, int* status,
+                            long long* blowup_step, const CheckArgs& c) {
     double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(k / a.nx), x = (int)(k - (long long)y * a.nx);
-        T dr = 0, jx = 0, jy = 0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const T g = Conv<S>::to_T(buf[src_offset(i, x, y, a)]);
-            dr += g;
-            jx += T(ex_of(i)) * g;
-            jy += T(ey_of(i)) * g;
-        }
-        jx += jx0;
-        jy += jy0;
-        const T r = T(a.rho0) + dr;
-        const T vx = jx / r, vy = jy / r;
-        if (isfinite(r) && isfinite(vx) && isfinite(vy)) {
-            const T u2 = vx * vx + vy * vy;
-            const T wx = vx - T(urefx), wy = vy - T(urefy);
-            acc[0] += (double)dr;
-            acc[1] += (double)jx;
-            acc[2] += (double)jy;
-            acc[3] += 0.5 * (double)(r * u2);
-            acc[4] += (double)u2;
-            acc[5] += (double)(wx * wx + wy * wy);
-            acc[6] = fmin(acc[6], (double)dr);
-        } else {
-            acc[7] += 1.0;
-        }
-    }
-    block_fold_partials(acc, partials);
-}
-
-// Pass 1: per-node rho, u in the collision precision T from the same vectorised pull gather
-// as the step kernel, accumulated per thread in FP64, then folded per block in a fixed
-// order.  Slots: 0 sum drho, 1 sum rho ux, 2 sum rho uy, 3 sum rho|u|^2/2, 4 sum |u|^2,
-// 5 sum |u-uref|^2, 6 min rho (as drho), 7 non-finite count.
-template <typename S>
-__global__ void __launch_bounds__(kBlock) reduce_kernel(const S* buf, FieldArgs a, double* partials,
-                                                        double urefx, double urefy) {
-    using T = typename Conv<S>::T;
-    constexpr int VEC = DefaultVec<S>::value;
-    const int lane = threadIdx.x & 31;
-    const int nseg = (a.nx + VEC - 1) / VEC;
-    const unsigned total = (unsigned)a.ny * (unsigned)nseg;
-    const unsigned stride = gridDim.x * blockDim.x;
-    const T jx0 = T(a.rho0 * a.urx), jy0 = T(a.rho0 * a.ury);
-    double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
-    for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
-        const unsigned s = base + lane;
-        const bool active = s < total;
-        const unsigned sc = active ? s : total - 1;
-        const int y = (int)(sc / (unsigned)nseg);
-        const int seg = (int)(sc - (unsigned)y * (unsigned)nseg);
-        const int x0 = seg * VEC;
-        const int nvalid = min(VEC, a.nx - x0);
-        T f[9][VEC];
-        gather_pull<S, VEC, 1>(buf, a.nx, a.ny, a.pitch, a.plane, y, seg, nseg, x0, nvalid, lane, f);
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            if (!active || j >= nvalid) continue;
-            T dr = 0, jx = 0, jy = 0;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                dr += f[i][j];
-                jx += T(ex_of(i)) * f[i][j];
-                jy += T(ey_of(i)) * f[i][j];
-            }
-            jx += jx0;
-            jy += jy0;
-            const T r = T(a.rho0) + dr;
-            const T vx = jx / r, vy = jy / r;
-            if (isfinite(r) && isfinite(vx) && isfinite(vy)) {
-                const T u2 = vx * vx + vy * vy;
-                const T wx = vx - T(urefx), wy = vy - T(urefy);
-                acc[0] += (double)dr;
-                acc[1] += (double)jx;
-                acc[2] += (double)jy;
-                acc[3] += 0.5 * (double)(r * u2);
-                acc[4] += (double)u2;
-                acc[5] += (double)(wx * wx + wy * wy);
-                acc[6] = fmin(acc[6], (double)dr);
-            } else {
-                acc[7] += 1.0;
-            }
-        }
-    }
-    block_fold_partials(acc, partials);
-}
-
-// Pass 2: one block folds the partials (fixed order), forms the outputs and applies the
-// blow-up criterion.
-__global__ void __launch_bounds__(kBlock) reduce_finish_kernel(const double* partials, int nparts, FieldArgs a,
-                                                               double* out, int* status, long long* blowup_step,
-                                                               CheckArgs c) {
-    __shared__ double sh[kBlock][kReduceValues];
-    double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
-    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+    for (int b = threadIdx.x; b < nparts; b += kReduceThreads) {
 #pragma unroll
         for (int v = 0; v < kReduceValues; ++v) {
-            const double x = partials[b * kReduceValues + v];
+            const double x = __ldcg(&partials[b * kReduceValues + v]);
             acc[v] = (v == 6) ? fmin(acc[v], x) : acc[v] + x;
         }
     }
-#pragma unroll
-    for (int v = 0; v < kReduceValues; ++v) sh[threadIdx.x][v] = acc[v];
+    __shared__ double tot[kReduceValues];
+    const double x = block_fold(acc);
+    if (threadIdx.x < kReduceValues) tot[threadIdx.x] = x;
     __syncthreads();
-    for (int s = kBlock / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) {
-#pragma unroll
-            for (int v = 0; v < kReduceValues; ++v)
-                sh[threadIdx.x][v] = (v == 6) ? fmin(sh[threadIdx.x][v], sh[threadIdx.x + s][v])
-                                              : sh[threadIdx.x][v] + sh[threadIdx.x + s][v];
-        }
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
         const double n = (double)a.nx * (double)a.ny;
-        const double* t = sh[0];
         double o[kReduceValues];
-        o[0] = n * a.rho0 + t[0];
-        o[1] = t[1];
-        o[2] = t[2];
-        o[3] = t[3];
-        o[4] = t[4] / n;
-        o[5] = t[5] / n;
-        o[6] = a.rho0 + t[6];
-        o[7] = t[7];
+        o[0] = n * a.rho0 + tot[0];
+        o[1] = tot[1];
+        o[2] = tot[2];
+        o[3] = tot[3];
+        o[4] = tot[4] / n;
+        o[5] = tot[5] / n;
+        o[6] = a.rho0 + tot[6];
+        o[7] = tot[7];
         for (int v = 0; v < kReduceValues; ++v) out[v] = o[v];
         if (c.apply && status && *status == 0) {
             const bool blown = (o[7] > 0.0) || !(o[6] > 0.0) ||
@@ -271,6 +168,175 @@ __global__ void __launch_bounds__(kBlock) reduce_finish_kernel(const double* par
             }
         }
     }
+}
+
+// Pass 1 arithmetic.  Per node: rho, j = sum xi f (+ rho0 u_ref) and u = j / rho in the
+// collision precision T.  The finite nodes' contributions are summed in T over kReduceFlush
+// consecutive row segments of a thread (in node order), then added to the thread's FP64
+// accumulators.  Slots: 0 sum drho, 1 sum rho ux, 2 sum rho uy, 3 sum rho|u|^2/2, 4 sum |u|^2,
+// 5 sum |u-uref|^2, 6 min rho (as drho), 7 non-finite count.  Both pass-1 kernels visit the
+// same segments in the same per-thread order, so their partials are bitwise equal.
+template <typename T> __device__ __forceinline__ T div_rho(T j, T ir, T r);
+template <> __device__ __forceinline__ float div_rho(float j, float ir, float) { return j * ir; }
+template <> __device__ __forceinline__ double div_rho(double j, double, double r) { return j / r; }
+
+template <typename T> struct SegSums {
+    T dr = 0, jx = 0, jy = 0, ke = 0, u2 = 0, w2 = 0, mn = T(INFINITY);
+    int good = 0, bad = 0;
+};
+
+template <typename T, int VEC>
+__device__ __forceinline__ void segment_add(const T (&f)[9][VEC], int nvalid, T rho0, T jx0, T jy0, T urefx,
+                                            T urefy, SegSums<T>& p) {
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        if (j >= nvalid) continue;
+        T dr = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            dr += f[i][j];
+            jx += T(ex_of(i)) * f[i][j];
+            jy += T(ey_of(i)) * f[i][j];
+        }
+        jx += jx0;
+        jy += jy0;
+        const T r = rho0 + dr;
+        const T ir = recip(r);
+        const T vx = div_rho(jx, ir, r), vy = div_rho(jy, ir, r);
+        if (isfinite(r) && isfinite(vx) && isfinite(vy)) {
+            const T u2 = vx * vx + vy * vy;
+            const T wx = vx - urefx, wy = vy - urefy;
+            p.dr += dr;
+            p.jx += jx;
+            p.jy += jy;
+            p.ke += r * u2;
+            p.u2 += u2;
+            p.w2 += wx * wx + wy * wy;
+            p.mn = fmin(p.mn, dr);
+            ++p.good;
+        } else {
+            ++p.bad;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void segment_flush(SegSums<T>& p, double (&acc)[kReduceValues]) {
+    if (p.good) {
+        acc[0] += (double)p.dr;
+        acc[1] += (double)p.jx;
+        acc[2] += (double)p.jy;
+        acc[3] += 0.5 * (double)p.ke;
+        acc[4] += (double)p.u2;
+        acc[5] += (double)p.w2;
+        acc[6] = fmin(acc[6], (double)p.mn);
+    }
+    const int bad = p.bad;
+    p = SegSums<T>();
+    p.bad = bad;
+}
+
+// End of pass 1: the block's partials; with a completion counter (FUSED), the last block to
+// finish also runs pass 2 and resets the counter for the next launch.
+template <bool FUSED>
+__device__ __forceinline__ void reduce_epilogue(double (&acc)[kReduceValues], double* partials, unsigned* counter,
+                                                const FieldArgs& a, double* out, int* status,
+                                                long long* blowup_step, const CheckArgs& c) {
+    const double x = block_fold(acc);
+    if (threadIdx.x < kReduceValues) partials[blockIdx.x * kReduceValues + threadIdx.x] = x;
+    if (!FUSED) return;
+    __shared__ bool last;
+    __threadfence();   // this block's partials before its count
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();   // every block's partials after the count
+    finish_fold(partials, gridDim.x, a, out, status, blowup_step, c);
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// Pass 1, scalar-load form for layouts whose rows are not 16-byte aligned (caller-owned
+// buffers of lbm_reduce_noalloc may have any pitch): the same row segments as the vectorised
+// form, one segment per thread and iteration.
+template <typename S, bool FUSED>
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel_scalar(const S* buf, FieldArgs a, double* partials,
+                                                                       unsigned* counter, double* out, int* status,
+                                                                       long long* blowup_step, CheckArgs c) {
+    using T = typename Conv<S>::T;
+    constexpr int VEC = DefaultVec<S>::value;
+    const int nseg = (a.nx + VEC - 1) / VEC;
+    const long long total = (long long)a.ny * nseg;
+    const T jx0 = T(a.rho0 * a.urx), jy0 = T(a.rho0 * a.ury);
+    double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
+    SegSums<T> p;
+    int it = 0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / nseg), seg = (int)(k - (long long)y * nseg);
+        const int x0 = seg * VEC;
+        const int nvalid = min(VEC, a.nx - x0);
+        T f[9][VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                f[i][j] = j < nvalid ? Conv<S>::to_T(buf[src_offset(i, x0 + j, y, a)]) : T(0);
+        }
+        segment_add<T, VEC>(f, nvalid, T(a.rho0), jx0, jy0, T(c.uref_x), T(c.uref_y), p);
+        if (++it == kReduceFlush) {
+            segment_flush(p, acc);
+            it = 0;
+        }
+    }
+    segment_flush(p, acc);
+    acc[7] = (double)p.bad;
+    reduce_epilogue<FUSED>(acc, partials, counter, a, out, status, blowup_step, c);
+}
+
+// Pass 1: the same vectorised pull gather as the step kernel, one row segment per thread and
+// iteration.
+template <typename S, bool FUSED>
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const S* buf, FieldArgs a, double* partials,
+                                                                unsigned* counter, double* out, int* status,
+                                                                long long* blowup_step, CheckArgs c) {
+    using T = typename Conv<S>::T;
+    constexpr int VEC = DefaultVec<S>::value;
+    const int lane = threadIdx.x & 31;
+    const int nseg = (a.nx + VEC - 1) / VEC;
+    const unsigned total = (unsigned)a.ny * (unsigned)nseg;
+    const unsigned stride = gridDim.x * blockDim.x;
+    const T jx0 = T(a.rho0 * a.urx), jy0 = T(a.rho0 * a.ury);
+    double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
+    SegSums<T> p;
+    int it = 0;
+    for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+        const unsigned s = base + lane;
+        const bool active = s < total;
+        const unsigned sc = active ? s : total - 1;
+        const int y = (int)(sc / (unsigned)nseg);
+        const int seg = (int)(sc - (unsigned)y * (unsigned)nseg);
+        const int x0 = seg * VEC;
+        const int nvalid = min(VEC, a.nx - x0);
+        T f[9][VEC];
+        gather_pull<S, VEC, 1>(buf, a.nx, a.ny, a.pitch, a.plane, y, seg, nseg, x0, nvalid, lane, f);
+        if (active) {
+            segment_add<T, VEC>(f, nvalid, T(a.rho0), jx0, jy0, T(c.uref_x), T(c.uref_y), p);
+            if (++it == kReduceFlush) {
+                segment_flush(p, acc);
+                it = 0;
+            }
+        }
+    }
+    segment_flush(p, acc);
+    acc[7] = (double)p.bad;
+    reduce_epilogue<FUSED>(acc, partials, counter, a, out, status, blowup_step, c);
+}
+
+// Pass 2 as its own launch (the allocation-free entry point, which keeps no counter).
+__global__ void __launch_bounds__(kReduceThreads) reduce_finish_kernel(const double* partials, int nparts, FieldArgs a,
+                                                                       double* out, int* status, long long* blowup_step,
+                                                                       CheckArgs c) {
+    finish_fold(partials, nparts, a, out, status, blowup_step, c);
 }
 
 int grid_for(long long n) {
@@ -297,21 +363,34 @@ cudaError_t gather_t(const void* buf, const FieldArgs& a, double* f, double* r, 
     return cudaGetLastError();
 }
 template <typename S>
-cudaError_t reduce_t(const void* buf, const FieldArgs& a, double* partials, double* out8, int* status,
-                     long long* blowup_step, const CheckArgs& c, cudaStream_t s) {
+cudaError_t reduce_t(const void* buf, const FieldArgs& a, double* partials, unsigned* counter, double* out8,
+                     int* status, long long* blowup_step, const CheckArgs& c, cudaStream_t s) {
     // the vectorised gather needs every row start 16-byte aligned
     const bool aligned = ((size_t)a.pitch * sizeof(S)) % 16 == 0 && ((uintptr_t)buf % 16) == 0;
+    const S* p = (const S*)buf;
+    if (counter) {
+        if (aligned)
+            reduce_kernel<S, true><<<kReduceBlocks, kReduceThreads, 0, s>>>(p, a, partials, counter, out8, status,
+                                                                          blowup_step, c);
+        else
+            reduce_kernel_scalar<S, true><<<kReduceBlocks, kReduceThreads, 0, s>>>(p, a, partials, counter, out8,
+                                                                                 status, blowup_step, c);
+        return cudaGetLastError();
+    }
     if (aligned)
-        reduce_kernel<S><<<kReduceBlocks, kBlock, 0, s>>>((const S*)buf, a, partials, c.uref_x, c.uref_y);
+        reduce_kernel<S, false><<<kReduceBlocks, kReduceThreads, 0, s>>>(p, a, partials, nullptr, out8, status,
+                                                                       blowup_step, c);
     else
-        reduce_kernel_scalar<S><<<kReduceBlocks, kBlock, 0, s>>>((const S*)buf, a, partials, c.uref_x, c.uref_y);
-    reduce_finish_kernel<<<1, kBlock, 0, s>>>(partials, kReduceBlocks, a, out8, status, blowup_step, c);
+        reduce_kernel_scalar<S, false><<<kReduceBlocks, kReduceThreads, 0, s>>>(p, a, partials, nullptr, out8,
+                                                                              status, blowup_step, c);
+    reduce_finish_kernel<<<1, kReduceThreads, 0, s>>>(partials, kReduceBlocks, a, out8, status, blowup_step, c);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 int reduce_blocks() { return kReduceBlocks; }
+size_t reduce_scratch_bytes() { return sizeof(double) * kReduceValues * kReduceBlocks + 16; }
 
 #define LBM_DISPATCH(storage, call)                                     \
     switch (storage) {                                                  \
@@ -333,9 +412,9 @@ cudaError_t launch_gather(int storage, const void* buf, const FieldArgs& a, doub
                           double* uy, double* pxx, double* pxy, double* pyy, cudaStream_t s) {
     LBM_DISPATCH(storage, gather_t<S>(buf, a, f, rho, ux, uy, pxx, pxy, pyy, s));
 }
-cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, double* partials, double* out8,
-                          int* status, long long* blowup_step, const CheckArgs& c, cudaStream_t s) {
-    LBM_DISPATCH(storage, reduce_t<S>(buf, a, partials, out8, status, blowup_step, c, s));
+cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, double* partials, unsigned* counter,
+                          double* out8, int* status, long long* blowup_step, const CheckArgs& c, cudaStream_t s) {
+    LBM_DISPATCH(storage, reduce_t<S>(buf, a, partials, counter, out8, status, blowup_step, c, s));
 }
 
 int storage_vec(int storage) {
@@ -424,7 +503,7 @@ extern "C" int lbm_reduce_noalloc(const void* populations, int storage, int nx, 
     c.ke_ref = 0.0; c.ke_factor = 1.0; c.uref_x = uref_x; c.uref_y = uref_y; c.step = 0; c.apply = 0;
     // pass 1 overwrites every partial slot before pass 2 reads it (same stream), so nothing in
     // the shared array needs clearing between calls
-    cudaError_t e = launch_reduce(storage, populations, a, scratch, out8, nullptr, nullptr, c,
+    cudaError_t e = launch_reduce(storage, populations, a, scratch, nullptr, out8, nullptr, nullptr, c,
                                   (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

@@ -54,14 +54,19 @@ cudaError_t launch_gather(int storage, const void* buf, const FieldArgs& a, doub
                           double* rho, double* ux, double* uy, double* pxx, double* pxy, double* pyy,
                           cudaStream_t s);
 // FP64 reductions: pass 1 writes `blocks` x 8 partials, pass 2 folds them into out[8] and
-// applies the blow-up criterion to status[0] (int) / blowup_step[0].
+// applies the blow-up criterion to status[0] (int) / blowup_step[0].  With a completion
+// counter (zero before the first launch; each launch leaves it zero) the last block of pass 1
+// runs pass 2 itself; without one, pass 2 is a second launch.
 struct CheckArgs {
     double ke_ref, ke_factor, uref_x, uref_y;
     long long step;
     int apply;       // evaluate the criterion
 };
 int reduce_blocks();
-cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, double* partials,
+// bytes of a context's reduction scratch: the partials, then the counter at offset
+// 8 * 8 * reduce_blocks()
+size_t reduce_scratch_bytes();
+cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, double* partials, unsigned* counter,
                           double* out8, int* status, long long* blowup_step, const CheckArgs& c,
                           cudaStream_t s);
 
