@@ -81,8 +81,10 @@ int lbm_rates_from_nu(double nu, int preset, lbm_rates* out);
  *   periodic  must be 1 (LBM_ERR_UNSUPPORTED otherwise)
  *   model     lbm_model; storage lbm_storage
  *   eq_order  4 = extended equilibrium (Eq. extendedFeq, default for every model);
+ *             3 = partial third-order equilibrium (Fig. 4: the extended one with its
+ *                 fourth-order Hermite moment A^eq_22 set to zero) and
  *             2 = second-order equilibrium (Sec. 2; Hermite moments of order >= 3 set to
- *                 zero), accepted for LBM_BGK only (LBM_ERR_UNSUPPORTED otherwise)
+ *                 zero), both accepted for LBM_BGK only (LBM_ERR_UNSUPPORTED otherwise)
  *   rho0      reference density of the shift g = f - w rho0 (normally 1)
  * Errors: nx, ny < 3, nx*ny > 2^31, rates outside (0,2), unknown enums -> INVALID_ARG;
  *         device allocation failure -> LBM_ERR_NOMEM.  *out is NULL on error. */
@@ -99,7 +101,7 @@ int lbm_set_rates(lbm_ctx* ctx, lbm_rates rates);
  * velocity; the default u_ref = 0 gives s_i = w_i rho0) and re-encode the current state.
  * Choosing u_ref near the flow's mean velocity keeps the stored deviations small, which
  * cuts the rounding error of FP16/BF16 storage.  Not a concept of the paper: a storage
- * detail.  Errors: non-finite or |u_ref| >= 1 -> INVALID_ARG; eq_order = 2 with u_ref != 0
+ * detail.  Errors: non-finite or |u_ref| >= 1 -> INVALID_ARG; eq_order 2 or 3 with u_ref != 0
  * -> UNSUPPORTED.  Waits on the context's stream. */
 int lbm_set_shift_velocity(lbm_ctx* ctx, double ux_ref, double uy_ref);
 
@@ -258,7 +260,7 @@ int lbm_group_timing(lbm_group* g, double* replay_ms, long long* lattice_steps, 
  * [forward ms incl. checkpoints, backward ms incl. recomputation].
  * The storage shift of lbm_set_shift_velocity is honoured (a shift at the mean flow keeps the
  * FP32 trajectory, and so its gradient, closer to FP64).
- * Errors: storage other than FP64/FP32, or eq_order 2 -> UNSUPPORTED. */
+ * Errors: storage other than FP64/FP32, or eq_order 2 or 3 -> UNSUPPORTED. */
 int lbm_adjoint_run(lbm_ctx* ctx, long long nsteps, int loss, const double* ux_target, const double* uy_target,
                     int checkpoint_every, double* grad_ux0, double* grad_uy0, double* grad_rates3,
                     double* loss_out, double* times_ms2);
@@ -317,7 +319,8 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 /* ---- Linear stability analysis (App. A) ---------------------------------------------
  * Growth rates of plane-wave perturbations of a uniform equilibrium state under the
  * stream-and-collide iteration: f'(x + xi_i, t + 1) = G f'(x, t), G = d f* / d f the Jacobian
- * of the collision map of `model` with `rates` at f = f^eq(rho, u) (Eq. extendedFeq), and for
+ * of the collision map of `model` with `rates` at f = f^eq(rho, u) of equilibrium order
+ * `eq_order` (as in lbm_create: 4 for every model, 2 or 3 for LBM_BGK only), and for
  * a wavenumber k the eigenproblem E^D(k) G A = exp(-i omega) A, E^D = diag(exp(-i xi_i . k))
  * (Eq. EigenvaluePbDiscrete).  G is the exact derivative of this library's own collision;
  * the eigenvalues come from a Hessenberg / shifted-QR solver in FP64 on the GPU.
@@ -327,11 +330,12 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  *           Im(omega) = ln |exp(-i omega)|
  *   eig     optional device, nflows x nk x 9 complex eigenvalues (re, im pairs)
  *   jac     optional device, nflows x 81 doubles: G row-major (G[i][j] = d f*_i / d f_j)
- * Synchronous on `stream`.  Errors: LBM_ERR_INVALID_ARG for an unknown model, a rate outside
- * (0, 2), a host pointer or more than 2^31 flow x wavenumber pairs; LBM_ERR_TIMEOUT if the QR
+ * Synchronous on `stream`.  Errors: LBM_ERR_INVALID_ARG for an unknown model or equilibrium
+ * order, a rate outside (0, 2), a host pointer or more than 2^31 flow x wavenumber pairs;
+ * LBM_ERR_UNSUPPORTED for eq_order 2 or 3 with a model other than BGK; LBM_ERR_TIMEOUT if the QR
  * iteration did not converge for some matrix (its growth entry is NaN); LBM_ERR_CUDA /
  * LBM_ERR_NOMEM.  PR uses omega3 = omega4 = 1 whatever `rates` says. */
-int lbm_lsa_growth(int model, lbm_rates rates, const double* flows, int nflows, const double* k, int nk,
+int lbm_lsa_growth(int model, lbm_rates rates, int eq_order, const double* flows, int nflows, const double* k, int nk,
                    double* growth, double* eig, double* jac, void* stream);
 
 /* Text of the last error on this context (never NULL); lbm_error_string names a code. */

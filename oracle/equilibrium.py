@@ -14,6 +14,14 @@ so the reading taken is the Hermite one: the equilibrium Hermite moments of orde
 vanish, A^eq_21 = A^eq_12 = A^eq_22 = 0, which is the textbook second-order polynomial
 equilibrium.  Converted to raw moments with Eq. HM2RM_Q9 this gives
     M21 = rho c_s^2 u_y,  M12 = rho c_s^2 u_x,  M22 = c_s^2 rho (u_x^2 + u_y^2) + rho c_s^4.
+
+partial third order ("order 3"): the middle truncation of Fig. 4, which Sec. 2 motivates by
+the third-order terms M^eq_21, M^eq_12 that correct the off-diagonal viscous stress.  Same
+Hermite reading: the equilibrium keeps A^eq_21 = rho u_x^2 u_y and A^eq_12 = rho u_x u_y^2 of
+the extended equilibrium and drops the fourth-order one, A^eq_22 = 0.  In raw moments M21
+and M12 are those of the extended equilibrium and
+    M22 = c_s^2 (M20 + M02) - c_s^4 rho = c_s^2 rho (u_x^2 + u_y^2) + rho c_s^4,
+i.e. the extended M22 minus rho u_x^2 u_y^2.
 """
 
 import numpy as np
@@ -23,8 +31,8 @@ from .moments import populations_from_raw
 
 
 def raw_equilibrium_moments(rho, ux, uy, order=4):
-    """Equilibrium raw moments M^eq_pq, p, q <= 2 (App. B after Eq. RMcoll; order 2 per
-    the reading in the module docstring)."""
+    """Equilibrium raw moments M^eq_pq, p, q <= 2 (App. B after Eq. RMcoll; orders 2 and 3
+    per the readings in the module docstring)."""
     M = {}
     M[0, 0] = rho
     M[1, 0] = rho * ux
@@ -36,12 +44,16 @@ def raw_equilibrium_moments(rho, ux, uy, order=4):
         M[2, 1] = M[2, 0] * uy
         M[1, 2] = ux * M[0, 2]
         M[2, 2] = M[2, 0] * M[0, 2] / rho
+    elif order == 3:
+        M[2, 1] = M[2, 0] * uy
+        M[1, 2] = ux * M[0, 2]
+        M[2, 2] = CS2 * (M[2, 0] + M[0, 2]) - CS2 * CS2 * rho
     elif order == 2:
         M[2, 1] = rho * CS2 * uy
         M[1, 2] = rho * CS2 * ux
         M[2, 2] = CS2 * rho * (ux * ux + uy * uy) + rho * CS2 * CS2
     else:
-        raise ValueError("equilibrium order must be 2 or 4")
+        raise ValueError("equilibrium order must be 2, 3 or 4")
     return M
 
 

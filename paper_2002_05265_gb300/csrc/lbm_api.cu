@@ -564,9 +564,9 @@ int lbm_create(lbm_ctx** out, int nx, int ny, int periodic, int model, lbm_rates
     if (nx < 3 || ny < 3 || (long long)nx * (long long)ny > (1LL << 31)) return LBM_ERR_INVALID_ARG;
     if (model < LBM_BGK || model > LBM_RR || storage < LBM_F64 || storage > LBM_BF16) return LBM_ERR_INVALID_ARG;
     if (!rates_ok(rates) || !(std::isfinite(rho0) && rho0 > 0.0)) return LBM_ERR_INVALID_ARG;
-    if (eq_order != 2 && eq_order != 4) return LBM_ERR_INVALID_ARG;
+    if (eq_order < 2 || eq_order > 4) return LBM_ERR_INVALID_ARG;
     if (periodic != 1) return LBM_ERR_UNSUPPORTED;
-    if (eq_order == 2 && model != LBM_BGK) return LBM_ERR_UNSUPPORTED;
+    if (eq_order != 4 && model != LBM_BGK) return LBM_ERR_UNSUPPORTED;
 
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_ERR_NOMEM;
@@ -639,7 +639,7 @@ int lbm_set_shift_velocity(lbm_ctx* c, double urx, double ury) {
     if (!c) return LBM_ERR_INVALID_ARG;
     if (!std::isfinite(urx) || !std::isfinite(ury) || std::fabs(urx) >= 1.0 || std::fabs(ury) >= 1.0)
         return set_err(c, LBM_ERR_INVALID_ARG, "shift velocity must be finite with |u| < 1");
-    if (c->eq_order == 2 && (urx != 0.0 || ury != 0.0))
+    if (c->eq_order != 4 && (urx != 0.0 || ury != 0.0))
         return set_err(c, LBM_ERR_UNSUPPORTED, "a shift velocity needs the extended equilibrium");
     if (urx == c->urx && ury == c->ury) return LBM_OK;
     // re-encode the current state: gather f with the old shift, scatter with the new one

@@ -40,7 +40,7 @@ __global__ void init_eq_kernel(S* buf, FieldArgs a, int eq_order, const double* 
         for (int i = 0; i < 9; ++i) {
             const int sx = ex_of(i), sy = ey_of(i);
             double g;
-            if (eq_order == 4) {
+            if (eq_order >= 3) {
                 // Eq. extendedFeq in product form minus the shift s_i = rho0 P_sx P_sy, with
                 // P_s = phi_s(u_ref) and D_s = phi_s(u) - phi_s(u_ref) written as differences
                 const double Px = phi1d(sx, a.urx), Py = phi1d(sy, a.ury);
@@ -48,6 +48,10 @@ __global__ void init_eq_kernel(S* buf, FieldArgs a, int eq_order, const double* 
                 const double Dx = sx ? 0.5 * dux * (sux + sx) : -dux * sux;
                 const double Dy = sy ? 0.5 * duy * (suy + sy) : -duy * suy;
                 g = Px * Py * dr + r * (Px * Dy + Dx * (Py + Dy));
+                // partial third order (u_ref = 0): minus rho u_x^2 u_y^2 times the populations
+                // of a unit M_22 (Eq. Q9postCollVDF_RM: 1 at rest, -1/2 on the axes, 1/4 on
+                // the diagonals)
+                if (eq_order == 3) g -= r * (vx * vx) * (vy * vy) * (sx ? -0.5 : 1.0) * (sy ? -0.5 : 1.0);
             } else {
                 const double wi = weight_of(i);
                 const double eu = 3.0 * (sx * vx + sy * vy);

@@ -211,7 +211,8 @@ __device__ __forceinline__ Consts<T> make_consts(const StepArgs& a) {
 // momentum change only by the rounding of D.  rho, ux, uy of the pre-collision state are
 // returned for diagnostics.  SHIFT = false is the default shift s = w rho0 (u_ref = 0), which
 // keeps the shift constants out of the arithmetic.  EQ = 2 (BGK only) uses the second-order
-// equilibrium of Sec. 2 in population space.
+// equilibrium of Sec. 2 in population space; EQ = 3 (BGK only) the partial third-order one of
+// Fig. 4 (Hermite A^eq_22 = 0: M^eq_22 without its rho u_x^2 u_y^2 term).
 template <int MODEL, int EQ, typename T, bool SHIFT>
 __device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], const Consts<T>& c, T& rho_out, T& ux_out,
                                         T& uy_out) {
@@ -287,6 +288,7 @@ __device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], const Consts
         n12 = m12 - (rho * ux) * Y;
         n22 = m22 - (drho * ((uxx + cs2) * Y) + c.rho0 * (uxx * Y + cs2 * uyy));
     }
+    if (EQ == 3) n22 += rho * (uxx * uyy);   // M^eq_22 of the partial third-order equilibrium
 
     // D = n - n* (the moments the collision removes), per model
     T D20, D02, D11, D21, D12, D22;
@@ -494,7 +496,7 @@ struct GroupEntry {
     void* dst;
     StepArgs a;
     int model;          // lbm::Model
-    int eq_order;       // 4, or 2 (BGK only)
+    int eq_order;       // 4, or 2 / 3 (BGK only)
     unsigned begin;     // first padded segment index of this lattice
     unsigned total;     // ny * nseg (unpadded)
 };
@@ -515,6 +517,7 @@ __device__ __forceinline__ void group_segment(const GroupEntry& e, const Consts<
     switch (e.model) {
         case BGK:
             if (e.eq_order == 2) step_segment<BGK, 2, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg);
+            else if (e.eq_order == 3) step_segment<BGK, 3, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg);
             else step_segment<BGK, 4, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg);
             break;
         case RM: step_segment<RM, 4, S, VEC, false, SH>(src, dst, e.a, c, s, e.total, lane, dg); break;

@@ -185,6 +185,39 @@ __global__ void lsa_jacobian_kernel(const double* __restrict__ flows, int nflows
     }
 }
 
+// G of BGK with the second-order (eq_order 2) or partial third-order (3) equilibrium, in
+// closed form: f*_i = f_i - omega (f_i - rho p_i(u)) with rho = sum f, u = sum xi f / rho, so
+// d f*_i / d f_j = (1 - omega) delta_ij + omega (p_i + dp_i/du_x (xi_jx - u_x) + dp_i/du_y (xi_jy - u_y)).
+//   order 2: p_i = w_i (1 + 3 xi.u + 9/2 (xi.u)^2 - 3/2 u^2) (Sec. 2, textbook polynomial);
+//   order 3: p_i = phi_sx(u_x) phi_sy(u_y) - u_x^2 u_y^2 b(sx) b(sy) (Eq. extendedFeq minus its
+//            A_22 term; b(0) = 1, b(+-1) = -1/2).
+__global__ void lsa_jacobian_bgk_kernel(const double* __restrict__ flows, int nflows, double omega, int eq_order,
+                                        double* __restrict__ G) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nflows) return;
+    const double ux = flows[3 * f + 1], uy = flows[3 * f + 2];
+    for (int i = 0; i < 9; ++i) {
+        const int sx = ex_of(i), sy = ey_of(i);
+        double p, px, py;
+        if (eq_order == 2) {
+            const double w = weight_of(i), eu = sx * ux + sy * uy;
+            p = w * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy));
+            px = w * (3.0 * sx + 9.0 * eu * sx - 3.0 * ux);
+            py = w * (3.0 * sy + 9.0 * eu * sy - 3.0 * uy);
+        } else {
+            const double fx = phi1d(sx, ux), fy = phi1d(sy, uy);
+            const double dfx = sx ? ux + 0.5 * sx : -2.0 * ux, dfy = sy ? uy + 0.5 * sy : -2.0 * uy;
+            const double b = (sx ? -0.5 : 1.0) * (sy ? -0.5 : 1.0);
+            p = fx * fy - ux * ux * uy * uy * b;
+            px = dfx * fy - 2.0 * ux * uy * uy * b;
+            py = fx * dfy - 2.0 * ux * ux * uy * b;
+        }
+        for (int j = 0; j < 9; ++j)
+            G[(long long)f * 81 + i * 9 + j] =
+                (i == j ? 1.0 - omega : 0.0) + omega * (p + px * (ex_of(j) - ux) + py * (ey_of(j) - uy));
+    }
+}
+
 // growth[f * nk + k] = max_j ln |lambda_j(E^D(k) G_f)|; eig (optional) the eigenvalues.
 __global__ void lsa_growth_kernel(const double* __restrict__ G, int nflows, const double* __restrict__ kvec, int nk,
                                   double* __restrict__ growth, double* __restrict__ eig, int* __restrict__ failed) {
@@ -235,12 +268,13 @@ bool on_device(const void* p) {
 }  // namespace
 }  // namespace lbm
 
-extern "C" int lbm_lsa_growth(int model, lbm_rates rates, const double* flows, int nflows, const double* k, int nk,
-                              double* growth, double* eig, double* jac, void* stream) {
+extern "C" int lbm_lsa_growth(int model, lbm_rates rates, int eq_order, const double* flows, int nflows,
+                              const double* k, int nk, double* growth, double* eig, double* jac, void* stream) {
     using namespace lbm;
     if (model < LBM_BGK || model > LBM_RR || !flows || !k || !growth || nflows < 1 || nk < 1 ||
-        (long long)nflows * nk > (1LL << 31))
+        (long long)nflows * nk > (1LL << 31) || eq_order < 2 || eq_order > 4)
         return LBM_ERR_INVALID_ARG;
+    if (eq_order != 4 && model != LBM_BGK) return LBM_ERR_UNSUPPORTED;
     const double r[3] = {rates.omega_nu, rates.omega3, rates.omega4};
     for (double w : r)
         if (!(std::isfinite(w) && w > 0.0 && w < 2.0)) return LBM_ERR_INVALID_ARG;
@@ -261,7 +295,10 @@ extern "C" int lbm_lsa_growth(int model, lbm_rates rates, const double* flows, i
     if (!G) e = cudaMalloc(&G, sizeof(double) * 81 * (size_t)nflows);
     if (e == cudaSuccess) e = cudaMalloc(&failed, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(failed, 0, sizeof(int), s);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && eq_order != 4) {
+        lsa_jacobian_bgk_kernel<<<(nflows + 127) / 128, 128, 0, s>>>(flows, nflows, rates.omega_nu, eq_order, G);
+        e = cudaGetLastError();
+    } else if (e == cudaSuccess) {
         switch (model) {
             case LBM_BGK: launch_jacobian<BGK>(flows, nflows, c, G, s); break;
             case LBM_RM: launch_jacobian<RM>(flows, nflows, c, G, s); break;

@@ -6,6 +6,7 @@ namespace lbm {
 template <typename S, bool SH>
 static const void* step_kernel_table_sh(int model, int eq_order) {
     if (eq_order == 2) return (model == BGK && !SH) ? (const void*)step_kernel<BGK, 2, S, false> : nullptr;
+    if (eq_order == 3) return (model == BGK && !SH) ? (const void*)step_kernel<BGK, 3, S, false> : nullptr;
     if (eq_order != 4) return nullptr;
     switch (model) {
         case BGK: return (const void*)step_kernel<BGK, 4, S, SH>;

@@ -82,7 +82,7 @@ struct TileEntry {
     unsigned cbase;     // first completion counter of this lattice (one per row or row block)
     StepArgs a;
     int model;          // lbm::Model
-    int eq_order;       // 4, or 2 (BGK only)
+    int eq_order;       // 4, or 2 / 3 (BGK only)
     int ntx;            // segment tiles: tiles per row, ceil(nx / W); row-block tiles: 0
     int rows;           // row-block tiles: rows per tile, floor(W / nx) >= 2; segment tiles: 1
     unsigned begin;     // first tile index of this lattice
@@ -308,6 +308,7 @@ __device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst,
     switch (E.model) {
         case BGK:
             if (E.eq_order == 2) tile_collide<BGK, 2, S, SHIFT>(stage, dst, E, q, p);
+            else if (E.eq_order == 3) tile_collide<BGK, 3, S, SHIFT>(stage, dst, E, q, p);
             else tile_collide<BGK, 4, S, SHIFT>(stage, dst, E, q, p);
             break;
         case RM: tile_collide<RM, 4, S, SHIFT>(stage, dst, E, q, p); break;

@@ -91,7 +91,7 @@ _SIGNATURES = {
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_error_string": (ctypes.c_char_p, [_I]),
     "lbm_version": (ctypes.c_char_p, []),
-    "lbm_lsa_growth": (_I, [_I, lbm_rates, _P, _I, _P, _I, _P, _P, _P, _P]),
+    "lbm_lsa_growth": (_I, [_I, lbm_rates, _I, _P, _I, _P, _I, _P, _P, _P, _P]),
 }
 
 
@@ -341,13 +341,13 @@ def lbm_batch_autotune(b, trial_steps=200, check_every=100):
     return v.value, k.value, ms.value
 
 
-def lbm_lsa_growth(model, rates, flows, k, growth, eig=None, jac=None, stream=None):
+def lbm_lsa_growth(model, rates, flows, k, growth, eig=None, jac=None, stream=None, eq_order=4):
     """flows: device (nflows, 3) doubles; k: device (nk, 2); growth: device (nflows, nk)."""
     if isinstance(model, str):
         model = MODELS[model]
     r = rates if isinstance(rates, lbm_rates) else lbm_rates(*rates)
     nflows, nk = int(flows.shape[0]), int(k.shape[0])
-    _check(load_library().lbm_lsa_growth(model, r, _addr(flows), nflows, _addr(k), nk, _addr(growth),
+    _check(load_library().lbm_lsa_growth(model, r, eq_order, _addr(flows), nflows, _addr(k), nk, _addr(growth),
                                          _addr(eig) if eig is not None else None,
                                          _addr(jac) if jac is not None else None, _stream(stream)))
 

@@ -34,13 +34,13 @@ def _flows(n, seed):
     return np.stack([g.uniform(0.9, 1.1, n), u * np.cos(phi), u * np.sin(phi)], axis=1)
 
 
-def _gpu(L, model, rates, flows, ks):
+def _gpu(L, model, rates, flows, ks, eq_order=4):
     fl = torch.from_numpy(np.ascontiguousarray(flows)).cuda()
     kk = torch.from_numpy(np.ascontiguousarray(ks)).cuda()
     growth = torch.empty((len(flows), len(ks)), dtype=torch.float64, device="cuda")
     eig = torch.empty((len(flows), len(ks), 9, 2), dtype=torch.float64, device="cuda")
     jac = torch.empty((len(flows), 9, 9), dtype=torch.float64, device="cuda")
-    L.lbm_lsa_growth(model, rates, fl, kk, growth, eig, jac)
+    L.lbm_lsa_growth(model, rates, fl, kk, growth, eig, jac, eq_order=eq_order)
     e = eig.cpu().numpy()
     return growth.cpu().numpy(), e[..., 0] + 1j * e[..., 1], jac.cpu().numpy()
 
@@ -64,6 +64,43 @@ def test_jacobian_and_growth_match_oracle(L, model, preset):
             d = np.abs(lam[:, None] - eig[f, k][None, :])
             assert np.max(np.min(d, axis=1)) <= 1e-10
             assert abs(growth[f, k] - np.max(np.log(np.abs(lam)))) <= 1e-10
+
+
+@pytest.mark.parametrize("eq_order", [2, 3])
+def test_truncated_equilibria_bgk_jacobian_and_growth(L, eq_order):
+    """BGK with the second-order or partial third-order equilibrium (closed-form Jacobian on
+    the GPU, complex step through the oracle's BGK): G within 1e-12, eigenvalues and growth
+    rates within 1e-10, on six base flows and twelve wavenumbers."""
+    rates = olbm.rates_from_nu(1e-3, "srt")
+    flows = _flows(6, seed=40 + eq_order)
+    ks = np.random.default_rng(7).uniform(-np.pi, np.pi, (12, 2))
+    growth, eig, jac = _gpu(L, "bgk", rates, flows, ks, eq_order)
+    for f, (rho, ux, uy) in enumerate(flows):
+        G = olsa.collision_map_jacobian("bgk", rho, ux, uy, rates, eq_order=eq_order)
+        assert np.max(np.abs(jac[f] - G)) <= 1e-12
+        for k, (kx, ky) in enumerate(ks):
+            lam = olsa.eigenvalues(G, kx, ky)
+            d = np.abs(lam[:, None] - eig[f, k][None, :])
+            assert np.max(np.min(d, axis=1)) <= 1e-10
+            assert abs(growth[f, k] - np.max(np.log(np.abs(lam)))) <= 1e-10
+
+
+def test_second_order_bgk_instability_bubble_on_gpu(L):
+    """Sec. 5a, Fig. 7: BGK with the second-order equilibrium at Ma = 0.1 (flow along x),
+    nu = 1e-5 grows near k = (0.1, 2.1); the partial third-order and the extended equilibria
+    do not; long waves stay stable (the same grids as the oracle's pin of this fact)."""
+    nu, Ma, kx0, ky0 = 1e-5, 0.1, 0.1, 2.1
+    w = 1.0 / (3.0 * nu + 0.5)
+    flows = np.array([[1.0, Ma / np.sqrt(3.0), 0.0]])
+    bubble = np.array([(a, b) for a in np.linspace(0.0, 2 * kx0, 41) for b in np.linspace(ky0 - 0.3, ky0 + 0.3, 25)])
+    g2, _, _ = _gpu(L, "bgk", (w, w, w), flows, bubble, 2)
+    g3, _, _ = _gpu(L, "bgk", (w, w, w), flows, bubble, 3)
+    g4, _, _ = _gpu(L, "bgk", (w, w, w), flows, bubble, 4)
+    assert np.max(g2) > 1e-4
+    assert np.max(g3) < 0.0 and np.max(g4) < 0.0
+    far = np.array([(a, b) for a in np.linspace(0, 0.5, 11) for b in np.linspace(0, 1.0, 11)])
+    g2f, _, _ = _gpu(L, "bgk", (w, w, w), flows, far, 2)
+    assert np.max(g2f) < 1e-12
 
 
 @pytest.mark.parametrize("model", ["bgk", "rm", "hm", "cm", "chm", "rr"])
@@ -102,6 +139,12 @@ def test_lsa_argument_checks(L):
     with pytest.raises(L.LBMError) as e:
         L.lbm_lsa_growth("bgk", (1.5, 1.0, 1.0), flows, kk, out)   # host flows
     assert e.value.code == L.LBM_ERR_INVALID_ARG
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_lsa_growth("bgk", (1.5, 1.0, 1.0), fl, kk, out, eq_order=5)
+    assert e.value.code == L.LBM_ERR_INVALID_ARG
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_lsa_growth("chm", (1.5, 1.0, 1.0), fl, kk, out, eq_order=3)
+    assert e.value.code == L.LBM_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("model", ["rm", "hm", "pr", "rr", "chm"])

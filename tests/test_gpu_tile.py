@@ -134,6 +134,48 @@ def test_bulk_multi_lattice_group(L):
         lat.close()
 
 
+@pytest.mark.parametrize("eq_order", [2, 3])
+def test_truncated_equilibria_every_kernel_family(L, eq_order):
+    """BGK with the second-order or partial third-order equilibrium on a 1100 x 6 FP64 lattice
+    (three tiles per row, the last short): the copy-engine and register-staged kernels within
+    1e-12 of the oracle after 40 steps; in a group with a CHM lattice (the group kernel), the
+    populations equal those of the lattice stepped alone."""
+    fields = flows.vortex(1100, 6, Ma=0.2, radius_frac=0.01, noise=1e-6, seed=17 + eq_order)
+    rates = olbm.rates_from_nu(1e-3, "srt")
+    ref = olbm.run(olbm.init_equilibrium(*fields, eq_order=eq_order), "bgk", rates, 40, eq_order=eq_order)
+    for path in (L.LBM_PATH_BULK, L.LBM_PATH_VECTOR):
+        lat = L.Lattice(1100, 6, L.LBM_BGK, rates, storage=L.LBM_F64, eq_order=eq_order)
+        lat.set_kernel_path(path)
+        lat.init_equilibrium(*_dev(*fields))
+        lat.step(40)
+        f = torch.empty((9, 6, 1100), dtype=torch.float64, device="cuda")
+        lat.get_populations(f)
+        lat.close()
+        got = f.cpu().numpy()
+        assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-12
+    other = flows.vortex(64, 33, Ma=0.2, noise=1e-6, seed=5)
+    lats = [L.Lattice(96, 40, L.LBM_BGK, rates, storage=L.LBM_F32, eq_order=eq_order),
+            L.Lattice(64, 33, L.LBM_CHM, rates, storage=L.LBM_F32)]
+    alone = L.Lattice(96, 40, L.LBM_BGK, rates, storage=L.LBM_F32, eq_order=eq_order)
+    f96 = flows.vortex(96, 40, Ma=0.2, noise=1e-6, seed=6)
+    for lat in (lats[0], alone):
+        lat.set_kernel_path(L.LBM_PATH_VECTOR)
+        lat.init_equilibrium(*_dev(*f96))
+    lats[1].set_kernel_path(L.LBM_PATH_VECTOR)
+    lats[1].init_equilibrium(*_dev(*other))
+    g = L.lbm_group_create([x.ctx for x in lats], graph_steps=8)
+    L.lbm_group_step(g, 24)
+    alone.step(24)
+    fa = torch.empty((9, 40, 96), dtype=torch.float64, device="cuda")
+    fb = torch.empty_like(fa)
+    lats[0].get_populations(fa)
+    alone.get_populations(fb)
+    assert torch.equal(fa, fb)
+    L.lbm_group_destroy(g)
+    for lat in lats + [alone]:
+        lat.close()
+
+
 def test_kernel_path_argument_checks(L):
     lat = L.Lattice(99, 10, L.LBM_BGK, (1.5, 1.5, 1.5), storage=L.LBM_F32)
     with pytest.raises(L.LBMError) as e:

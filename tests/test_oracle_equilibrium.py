@@ -81,6 +81,58 @@ def test_second_order_equilibrium_matches_only_low_moments():
             assert np.max(np.abs(lhs - rhs)) > 1e-3
 
 
+def test_third_order_equilibrium_matches_all_moments_but_m22():
+    """Partial third order (Fig. 4, middle): the matching conditions of every p, q <= 2 but
+    (2, 2) hold -- M_21 and M_12 included, which correct the off-diagonal viscous stress
+    (Sec. 2) -- and M_22 misses the Maxwellian's by exactly rho u_x^2 u_y^2."""
+    rho, ux, uy = _fields()
+    f = equilibrium.feq(rho, ux, uy, 3)
+    for (p, q) in d2q9.PQ:
+        lhs = sum(d2q9.XI[i, 0] ** p * d2q9.XI[i, 1] ** q * f[i] for i in range(9))
+        rhs = _maxwellian_moment(rho, ux, uy, p, q)
+        if (p, q) == (2, 2):
+            np.testing.assert_allclose(rhs - lhs, rho * ux ** 2 * uy ** 2, rtol=0, atol=1e-15)
+        else:
+            np.testing.assert_allclose(lhs, rhs, rtol=0, atol=1e-15)
+
+
+def test_third_order_equilibrium_is_the_truncated_hermite_expansion():
+    """The D2Q9 Hermite expansion of the Maxwellian truncated after the mixed third-order
+    terms, written out from the tensor Hermite polynomials:
+    w_i [rho + rho xi.u / c_s^2 + (H2 : rho u u) / (2 c_s^4) + (H_xxy a_xxy + H_xyy a_xyy) / (2 c_s^6)]
+    with a_xxy = rho u_x^2 u_y, a_xyy = rho u_x u_y^2 (3!/(3! c_s^6) times three equal
+    permutations gives 1/(2 c_s^6)); its fourth-order Hermite moment is zero."""
+    rho, ux, uy = _fields()
+    f = equilibrium.feq(rho, ux, uy, 3)
+    cs2 = d2q9.CS2
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    for i in range(9):
+        x, y = d2q9.XI[i]
+        h2 = (x * x - cs2) * ux * ux + 2 * x * y * ux * uy + (y * y - cs2) * uy * uy
+        hxxy, hxyy = (x * x - cs2) * y, x * (y * y - cs2)
+        ref = w[i] * rho * (1 + (x * ux + y * uy) / cs2 + h2 / (2 * cs2 ** 2)
+                            + (hxxy * ux * ux * uy + hxyy * ux * uy * uy) / (2 * cs2 ** 3))
+        np.testing.assert_allclose(f[i], ref, rtol=0, atol=2e-16)
+    a22 = sum((d2q9.XI[i, 0] ** 2 - cs2) * (d2q9.XI[i, 1] ** 2 - cs2) * f[i] for i in range(9))
+    np.testing.assert_allclose(a22, 0.0, atol=1e-16)
+
+
+def test_equilibria_differ_by_their_truncated_hermite_terms():
+    """Extended - third order = rho u_x^2 u_y^2 times the population vector of a unit M_22
+    (Eq. Q9postCollVDF_RM: +1 at rest, -1/2 on the axes, +1/4 on the diagonals); all three
+    orders coincide at rest (w_i rho)."""
+    rho, ux, uy = _fields()
+    d = equilibrium.feq(rho, ux, uy, 4) - equilibrium.feq(rho, ux, uy, 3)
+    beta = {0: 1.0, 1: -0.5, -1: -0.5}
+    for i in range(9):
+        x, y = (int(v) for v in d2q9.XI[i])
+        np.testing.assert_allclose(d[i], rho * ux ** 2 * uy ** 2 * beta[x] * beta[y], rtol=0, atol=2e-16)
+    z = np.zeros(3)
+    r = np.array([0.9, 1.0, 1.1])
+    for order in (2, 3):
+        np.testing.assert_allclose(equilibrium.feq(r, z, z, order), equilibrium.feq(r, z, z, 4), rtol=0, atol=1e-16)
+
+
 def test_product_form_equals_moment_form():
     """The two equalities of Eq. extendedFeq agree."""
     rho, ux, uy = _fields()
