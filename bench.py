@@ -477,7 +477,8 @@ def run_transport(args):
 
 def run_lsa_map(args):
     """Linear stability curves of the stream-and-collide scheme (Sec. 4c, App. A): for every
-    model in both rate presets and nu in 1e-6 .. 1e-1, the largest Mach number (bisection to
+    model in both rate presets (and BGK with the second-order and partial third-order
+    equilibria) and nu in 1e-6 .. 1e-1, the largest Mach number (bisection to
     1e-3) for which no plane wave grows, max over a K x K wavenumber grid on [-pi, pi]^2 and 16
     mean-flow angles phi in [0, pi/4] (the D2Q9 symmetries cover the rest) of
     Im(omega) <= 1e-10 (the conserved modes at k = 0 have exactly 0).  Uses lbm_lsa_growth (the
@@ -494,33 +495,49 @@ def run_lsa_map(args):
     growth = torch.empty((len(phis), K * K), dtype=torch.float64, device="cuda")
     calls, t0 = 0, time.perf_counter()
 
-    def unstable(m, rates, ma):
+    def unstable(m, rates, ma, eq_order):
         u = ma * CS
         fl = torch.from_numpy(np.stack([np.ones_like(phis), u * np.cos(phis), u * np.sin(phis)], axis=1)).cuda()
-        lbm.lbm_lsa_growth(m, rates, fl, ks, growth)
+        lbm.lbm_lsa_growth(m, rates, fl, ks, growth, eq_order=eq_order)
         return float(growth.max()) > 1e-10
 
-    for m, preset in MAP_CONFIGS:
+    # BGK with the second-order and partial third-order equilibria first (the lattice
+    # counterpart of Fig. 4's three truncations), then every model with the extended one
+    configs = [("bgk", "srt", 2), ("bgk", "srt", 3)] + [(m, c, 4) for m, c in MAP_CONFIGS]
+    for m, preset, eq_order in configs:
         for nu in nus:
             w = 1.0 / (3.0 * nu + 0.5)
             rates = (w, w, w) if preset == "srt" else (w, 1.0, 1.0)
-            if unstable(m, rates, 0.0):
+            if unstable(m, rates, 0.0, eq_order):
                 ma_max = 0.0
             else:
                 lo, hi = 0.0, 1.0
                 while hi - lo > 1e-3:
                     mid = 0.5 * (lo + hi)
-                    if unstable(m, rates, mid):
+                    if unstable(m, rates, mid, eq_order):
                         hi = mid
                     else:
                         lo = mid
                     calls += 1
                 ma_max = lo
             calls += 1
-            print(json.dumps({"lsa": True, "model": m, "preset": preset, "nu": nu, "ma_max": round(ma_max, 4),
-                              "k_grid": K, "angles": len(phis)}), flush=True)
+            print(json.dumps({"lsa": True, "model": m, "preset": preset, "eq_order": eq_order, "nu": nu,
+                              "ma_max": round(ma_max, 4), "k_grid": K, "angles": len(phis)}), flush=True)
     dt = time.perf_counter() - t0
     print(json.dumps({"lsa_summary": True, "calls": calls, "matrices": calls * len(phis) * K * K, "seconds": dt}))
+    # Fig. 7 (right): BGK at Ma = 0.1 along x, nu = 1e-5, growth-rate map over k in [0, pi]^2
+    # (512 x 512), per equilibrium order: the largest growth rate and where it is
+    k2 = np.linspace(0.0, np.pi, 512)
+    kk = torch.from_numpy(np.array([(a, b) for a in k2 for b in k2])).cuda()
+    g2 = torch.empty((1, kk.shape[0]), dtype=torch.float64, device="cuda")
+    w = 1.0 / (3.0 * 1e-5 + 0.5)
+    fl = torch.tensor([[1.0, 0.1 * CS, 0.0]], dtype=torch.float64, device="cuda")
+    for eq_order in (2, 3, 4):
+        lbm.lbm_lsa_growth("bgk", (w, w, w), fl, kk, g2, eq_order=eq_order)
+        i = int(torch.argmax(g2))
+        print(json.dumps({"lsa_fig7": True, "model": "bgk", "eq_order": eq_order, "Ma": 0.1, "nu": 1e-5,
+                          "max_growth": float(g2.max()), "at_k": [float(kk[i, 0]), float(kk[i, 1])],
+                          "unstable_fraction": float((g2 > 1e-10).double().mean())}))
 
 
 def run_accuracy(args):
