@@ -18,7 +18,7 @@ constexpr int kBlock = 256;
 constexpr int kReduceBlocks = 608;   // 4 x 152 SMs; fixed, so the fold order is deterministic
 constexpr int kReduceThreads = 128;  // threads of a reduction block (fewer threads, less FP64 folding)
 constexpr int kReduceValues = 8;
-constexpr int kReduceFlush = 2;      // row segments summed in the collision precision per FP64 add
+constexpr int kReduceFlush = 4;      // row segments summed in the collision precision per FP64 add
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -109,27 +109,52 @@ __global__ void gather_kernel(const S* buf, FieldArgs a, double* f, double* rho,
     }
 }
 
+__device__ __forceinline__ double fold_op(int slot, double x, double y) { return slot == 6 ? fmin(x, y) : x + y; }
+
+// Folds the eight values of the 32 lanes of a warp (slot 6 by min, the others by sum) with
+// nine FP64 operations a lane: in the rounds xor 16, 8 and 4 every lane keeps half of the
+// slots it still holds and adds its partner's copy of them, then the rounds xor 2 and 1 fold
+// the one slot left.  Lane l ends with the warp's value of slot
+// 4 * bit4(l) + 2 * bit3(l) + bit2(l); *slot_out is that slot.
+__device__ __forceinline__ double warp_fold8(const double (&a)[kReduceValues], int lane, int* slot_out) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    const int base = h16 ? 4 : 0;
+    double b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const double recv = __shfl_xor_sync(0xffffffffu, h16 ? a[j] : a[j + 4], 16);
+        b[j] = fold_op(base + j, h16 ? a[j + 4] : a[j], recv);
+    }
+    const int base2 = base + (h8 ? 2 : 0);
+    double c[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const double recv = __shfl_xor_sync(0xffffffffu, h8 ? b[j] : b[j + 2], 8);
+        c[j] = fold_op(base2 + j, h8 ? b[j + 2] : b[j], recv);
+    }
+    const int slot = base2 + (h4 ? 1 : 0);
+    double d = fold_op(slot, h4 ? c[1] : c[0], __shfl_xor_sync(0xffffffffu, h4 ? c[0] : c[1], 4));
+    d = fold_op(slot, d, __shfl_xor_sync(0xffffffffu, d, 2));
+    d = fold_op(slot, d, __shfl_xor_sync(0xffffffffu, d, 1));
+    *slot_out = slot;
+    return d;
+}
+
 // Folds the per-thread values acc[0..7] of a block of kReduceThreads threads in a fixed order
-// (warp shuffles, then the warps in order; slot 6 by min, the others by sum); thread v < 8
-// returns the block's value v, the other threads return 0.
+// (the warp fold above, then the warps in order); thread v < 8 returns the block's value v,
+// the other threads return 0.
 __device__ __forceinline__ double block_fold(const double (&acc)[kReduceValues]) {
     __shared__ double sh[kReduceThreads / 32][kReduceValues];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int v = 0; v < kReduceValues; ++v) {
-        double x = acc[v];
-        for (int o = 16; o > 0; o >>= 1) {
-            const double y2 = __shfl_down_sync(0xffffffffu, x, o);
-            x = (v == 6) ? fmin(x, y2) : x + y2;
-        }
-        if (lane == 0) sh[warp][v] = x;
-    }
+    int slot;
+    const double w = warp_fold8(acc, lane, &slot);
+    if ((lane & 3) == 0) sh[warp][slot] = w;
     __syncthreads();
     double x = 0.0;
     if (threadIdx.x < kReduceValues) {
         const int v = threadIdx.x;
         x = sh[0][v];
-        for (int w = 1; w < kReduceThreads / 32; ++w) x = (v == 6) ? fmin(x, sh[w][v]) : x + sh[w][v];
+        for (int k = 1; k < kReduceThreads / 32; ++k) x = fold_op(v, x, sh[k][v]);
     }
     return x;
 }
@@ -140,12 +165,20 @@ __device__ __forceinline__ double block_fold(const double (&acc)[kReduceValues])
 __device__ void finish_fold(const double* partials, int nparts, const FieldArgs& a, double* out, int* status,
                             long long* blowup_step, const CheckArgs& c) {
     double acc[kReduceValues] = {0, 0, 0, 0, 0, 0, 1e300, 0};
-    for (int b = threadIdx.x; b < nparts; b += kReduceThreads) {
+    // nparts <= kReduceBlocks: a fixed trip count, so the loads of every round issue together
+    constexpr int kRounds = (kReduceBlocks + kReduceThreads - 1) / kReduceThreads;
+    double part[kRounds][kReduceValues];
 #pragma unroll
-        for (int v = 0; v < kReduceValues; ++v) {
-            const double x = __ldcg(&partials[b * kReduceValues + v]);
-            acc[v] = (v == 6) ? fmin(acc[v], x) : acc[v] + x;
-        }
+    for (int k = 0; k < kRounds; ++k) {
+        const int b = threadIdx.x + k * kReduceThreads;
+#pragma unroll
+        for (int v = 0; v < kReduceValues; ++v)
+            part[k][v] = b < nparts ? __ldcg(&partials[b * kReduceValues + v]) : acc[v];
+    }
+#pragma unroll
+    for (int k = 0; k < kRounds; ++k) {
+#pragma unroll
+        for (int v = 0; v < kReduceValues; ++v) acc[v] = fold_op(v, acc[v], part[k][v]);
     }
     __shared__ double tot[kReduceValues];
     const double x = block_fold(acc);

@@ -193,6 +193,26 @@ def test_moments_and_reductions_match_oracle(L):
     lat.close()
 
 
+def test_successive_checks_reset_the_completion_counter(L):
+    """lbm_reduce runs its second pass in the last block of the first launch (a completion
+    counter that every launch leaves at zero): 25 successive reductions of an evolving FP64
+    lattice, three steps apart, each equal the oracle's reductions of the same populations."""
+    fields = flows.vortex(40, 33, Ma=0.2, noise=1e-6, seed=8)
+    rates = olbm.rates_from_nu(1e-3, "reg")
+    lat = L.Lattice(40, 33, L.LBM_K, rates, storage=L.LBM_F64)
+    lat.init_equilibrium(*_dev(*fields))
+    lat.set_check(0, uref=(0.05, 0.01))
+    red = torch.empty(8, dtype=torch.float64, device="cuda")
+    f = torch.empty((9, 33, 40), dtype=torch.float64, device="cuda")
+    for _ in range(25):
+        lat.step(3)
+        lat.reduce(red)
+        lat.get_populations(f)
+        np.testing.assert_allclose(red.cpu().numpy(), olbm.reductions(f.cpu().numpy(), (0.05, 0.01)),
+                                   rtol=1e-12, atol=1e-14)
+    lat.close()
+
+
 def test_host_and_device_pointers_agree(L):
     fields = flows.vortex(32, Ma=0.2, noise=1e-6, seed=5)
     rates = olbm.rates_from_nu(1e-3)
