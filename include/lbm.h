@@ -126,7 +126,11 @@ int lbm_moments(lbm_ctx* ctx, double* rho, double* ux, double* uy,
  *   [3] sum rho |u|^2 / 2  [4] <|u|^2>              [5] <|u - uref|^2>
  *   [6] min rho            [7] number of nodes with non-finite rho or u
  * (<.> = mean over nodes; uref set by lbm_set_check).  Per-node values are computed in the
- * collision precision, sums are accumulated in FP64 in a fixed order (deterministic). */
+ * collision precision and summed in it over the four row segments a thread visits in a row
+ * of its loop (8 nodes for FP64, 16 for FP32, 32 for 16-bit storage); those partial sums are
+ * accumulated in FP64 in a fixed order (deterministic).  One launch: the last block to finish folds the per-block
+ * partials, using a completion counter that the context owns and every launch leaves at zero.
+ * Calls on one context must not overlap on the GPU (they share that scratch). */
 int lbm_reduce(lbm_ctx* ctx, double* out8);
 
 /* lbm_reduce without any allocation, for a population buffer the caller owns.

@@ -209,8 +209,8 @@ __device__ void finish_fold(const double* partials, int nparts, const FieldArgs&
 
 // Pass 1 arithmetic.  Per node: rho, j = sum xi f (+ rho0 u_ref) and u = j / rho in the
 // collision precision T.  The finite nodes' contributions are summed in T over kReduceFlush
-// consecutive row segments of a thread (in node order), then added to the thread's FP64
-// accumulators.  Slots: 0 sum drho, 1 sum rho ux, 2 sum rho uy, 3 sum rho|u|^2/2, 4 sum |u|^2,
+// successive row segments of a thread's grid-stride loop (in node order), then added to the
+// thread's FP64 accumulators.  Slots: 0 sum drho, 1 sum rho ux, 2 sum rho uy, 3 sum rho|u|^2/2, 4 sum |u|^2,
 // 5 sum |u-uref|^2, 6 min rho (as drho), 7 non-finite count.  Both pass-1 kernels visit the
 // same segments in the same per-thread order, so their partials are bitwise equal.
 template <typename T> __device__ __forceinline__ T div_rho(T j, T ir, T r);
