@@ -827,8 +827,9 @@ def main():
 
     # step-kernel launches counted by the group's replay timing (one multi-step launch per
     # replay for the bulk-copy kernel, one per time step otherwise), plus per lattice: the
-    # equilibrium init, two reduction kernels per check, the moments gather
-    launches_per_step = kernel_launches // args.steps + len(MODELS) * (1 + 2 * (S // CHECK_EVERY) + 1)
+    # equilibrium init, one reduction kernel per check (its last block folds the partials),
+    # the moments gather
+    launches_per_step = kernel_launches // args.steps + len(MODELS) * (1 + (S // CHECK_EVERY) + 1)
 
     e2e = None
     if not args.no_e2e:
