@@ -302,6 +302,19 @@ def adjoint_ratio(lbm, flows, stream, path=0, stages=0):
     return {"workload": "512x512 vortex, 4000 steps, FP32, REG rates, misfit loss, 64 checkpoints", "models": res}
 
 
+METRIC = "D2Q9 lattice updates per second, 8 collision models (GLUPS)"
+
+
+def bench_config(S, world):
+    """The benchmark workload's `config` (both arms report the same one)."""
+    return {"workload": f"double shear layer {L}x{L}, Ma={MA}, nu={NU}, {S} steps per lattice, "
+                        f"8 collision models (BGK, RM, HM, CM, CHM, K, PR, RR), FP32 shifted storage",
+            "lattices": len(MODELS), "lattice": f"{L}x{L}", "sim_steps": S,
+            "check_every": CHECK_EVERY, "graph_steps": GRAPH_STEPS,
+            "l2": "inputs larger than L2: 8 lattices x 75.5 MB advanced in turn each time step",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -332,16 +345,15 @@ def run_reference(args, rank, world):
     t0 = time.perf_counter()
     olbm.run(olbm.init_equilibrium(*vf), "bgk", olbm.rates_from_nu(1e-4, "srt"), 1000)
     vortex_s = time.perf_counter() - t0
-    out = {"impl": "reference", "metric": "D2Q9 lattice updates per second, 8 collision models",
+    out = {"impl": "reference", "metric": METRIC,
            "value": v, "unit": "GLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"double shear layer {L}x{L}, 8 models, one time step per model per step "
-                                  f"(bounded sample of the {args.sim_steps}-step run)",
-                      "lattice": f"{L}x{L}", "models": MODELS},
+           "config": bench_config(args.sim_steps, world),
            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": procs, "host_cores": os.cpu_count(), "kind": "oracle",
-                            "sample": "one time step of each of the 8 models per benchmark step, the models in "
-                                      f"{procs} parallel single-threaded numpy processes"},
+                            "sample": "each benchmark step a bounded sample of the workload: one time step of "
+                                      f"each of the 8 models on its {L}x{L} lattice (not {args.sim_steps}), "
+                                      f"the models in {procs} parallel single-threaded numpy processes"},
            "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "single_process": {"per_model_mlups_1024": per_model, "vortex_128_bgk_1000_steps_seconds": vortex_s}}
     print(json.dumps(out))
@@ -876,16 +888,11 @@ def main():
         cpu = cpu_baseline()
 
     if rank == 0:
-        out = {"metric": "D2Q9 lattice updates per second, 8 collision models (GLUPS)",
+        out = {"metric": METRIC,
                "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": f"double shear layer {L}x{L}, Ma={MA}, nu={NU}, {S} steps per lattice, "
-                                      f"8 collision models (BGK, RM, HM, CM, CHM, K, PR, RR), FP32 shifted storage",
-                          "lattices": len(MODELS), "lattice": f"{L}x{L}", "sim_steps": S,
-                          "check_every": CHECK_EVERY, "graph_steps": GRAPH_STEPS,
-                          "l2": "inputs larger than L2: 8 lattices x 75.5 MB advanced in turn each time step",
-                          "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+               "config": bench_config(S, world),
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock_info,
                "gpu_launches": launches_per_step * args.steps,
                "blowup": {m: (s[1] if s[0] != 0 else None) for m, s in statuses.items()}}
