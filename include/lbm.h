@@ -149,17 +149,24 @@ int lbm_reduce(lbm_ctx* ctx, double* out8);
  *                x - xi_i (periodic), i.e. the state that the next pull step would read
  *   nx, ny       lattice size, 3 <= nx <= pitch, ny >= 3, nx * ny <= 2^31 (larger lattices
  *                are rejected with LBM_ERR_INVALID_ARG)
- *   uref_x/_y    reference velocity of out[5]
+ *   uref_x/_y    reference velocity of out[5] only.  The buffer is always decoded with the
+ *                w_i rho0 shift (storage-shift velocity zero): a buffer written by a
+ *                context after lbm_set_shift_velocity with a non-zero velocity holds
+ *                f_i - f^eq_i(rho0, u_ref) and is NOT supported -- its rho, momentum and
+ *                blow-up figures would come out wrong without any error
  *   out8         device pointer to 8 doubles, same meaning as lbm_reduce (host pointers are
  *                rejected: copying them back would need staging memory)
  *   cuda_stream  stream to run on (NULL = legacy default stream); asynchronous
- * Returns LBM_ERR_INVALID_ARG for a null, misaligned or non-device pointer, an unknown
- * storage or out-of-range sizes, LBM_ERR_CUDA if a launch fails.
+ * Both buffers must be on the current device (or managed memory).  Returns
+ * LBM_ERR_INVALID_ARG for a null, misaligned or non-device pointer, a pointer to another
+ * GPU's memory, an unknown storage or out-of-range sizes, LBM_ERR_CUDA if a launch fails.
  *
  * Scratch: the per-block partial sums go to one file-scope device array of 608 x 8 doubles
  * (38,912 bytes), which every GPU that loads the library holds until the process exits.  The
  * first call on each device looks up that array's device address (cudaGetSymbolAddress) with
  * the device current; make that first call before any stream capture that could contain it.
+ * The address is kept per device ordinal for the life of the process, so do not call this
+ * after cudaDeviceReset on that device (the array of the new context has another address).
  * All calls share the array: calls that overlap on the GPU (e.g. on two streams at once)
  * race and give wrong results.  Each call rewrites every partial before reading it, so no
  * call depends on what the previous one left there.  No cudaMalloc, cudaFree or other

@@ -491,13 +491,17 @@ static __device__ __align__(256) double g_noalloc_partials[kReduceBlocks * kRedu
 std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
 
-bool noalloc_is_device_ptr(const void* p) {
+// Device memory of device `dev` (the current one), or managed memory.  Device memory of
+// another GPU is rejected: the kernels run on the current device, and reading another GPU's
+// memory without peer access enabled is an illegal access.
+bool noalloc_is_device_ptr(const void* p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 }  // namespace
 
@@ -515,10 +519,10 @@ extern "C" int lbm_reduce_noalloc(const void* populations, int storage, int nx, 
         return LBM_ERR_INVALID_ARG;
     const size_t esize = (size_t)storage_bytes(storage);
     if (((uintptr_t)populations % esize) != 0 || ((uintptr_t)out8 % sizeof(double)) != 0) return LBM_ERR_INVALID_ARG;
-    if (!noalloc_is_device_ptr(populations) || !noalloc_is_device_ptr(out8)) return LBM_ERR_INVALID_ARG;
-
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return LBM_ERR_CUDA;
+    if (!noalloc_is_device_ptr(populations, dev) || !noalloc_is_device_ptr(out8, dev)) return LBM_ERR_INVALID_ARG;
+
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
