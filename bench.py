@@ -52,7 +52,10 @@ def parse():
     p.add_argument("--sim-steps", type=int, default=SIM_STEPS)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-per-model", action="store_true", help="skip the per-model 4096^2 timing")
+    p.add_argument("--no-per-model", action="store_true",
+                   help="skip the per-model x storage timing on the 16384^2 vortex")
+    p.add_argument("--no-batch-key", action="store_true", help="skip the bounded batched-sweep measurement")
+    p.add_argument("--no-accuracy-key", action="store_true", help="skip the storage-accuracy table")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint / forward time ratio")
     p.add_argument("--batch", action="store_true",
                    help="instead of the benchmark step, run the batched stability sweep (4096 lattices)")
@@ -213,6 +216,7 @@ def ncu_traffic(kernel_tag):
 
 
 _ORACLE_F0 = None
+CPU_SLAB = 128   # rows per oracle task (L / CPU_SLAB tasks per model and time step)
 
 
 def _oracle_init():
@@ -223,48 +227,65 @@ def _oracle_init():
     _ORACLE_F0 = olbm.init_equilibrium(*flows.double_shear_layer(L, Ma=MA))
 
 
-def _oracle_step(model):
-    """One oracle time step of one collision model (the result is discarded)."""
+def oracle_slab_step(f, model, rates, y0, rows):
+    """One oracle time step of one collision model on rows y0 .. y0 + rows - 1 of the
+    population field f[9][ny][nx]: the oracle steps the slab plus one halo row on each side
+    (periodic in x), which gives those rows exactly what a step of the whole lattice gives
+    them (a stream-and-collide step reaches one node).  Returns the slab's own rows."""
     import oracle.lbm as olbm
-    olbm.step(_ORACLE_F0, model, olbm.rates_from_nu(NU, _preset(model)))
-    return model
+    idx = np.arange(y0 - 1, y0 + rows + 1) % f.shape[1]
+    return olbm.step(f[:, idx, :], model, rates)[:, 1:-1, :]
+
+
+def _oracle_slab_step(task):
+    """Worker task: one time step of one model on one CPU_SLAB-row slab of the benchmark
+    lattice (the result is discarded); returns the lattice updates of the slab's rows."""
+    import oracle.lbm as olbm
+    model, y0 = task
+    oracle_slab_step(_ORACLE_F0, model, olbm.rates_from_nu(NU, _preset(model)), y0, CPU_SLAB)
+    return CPU_SLAB * L
 
 
 def oracle_pool():
-    """Worker processes for the oracle timing, one per model up to the host's cores; spawned
-    (not forked), so a process that already holds a CUDA context can start them."""
+    """Worker processes for the oracle timing, one per host core; spawned (not forked), so
+    a process that already holds a CUDA context can start them."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
-    procs = max(1, min(len(MODELS), os.cpu_count() or 1))
+    procs = max(1, os.cpu_count() or 1)
     return ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn"), initializer=_oracle_init), procs
 
 
+ORACLE_TASKS = [(m, y0) for m in MODELS for y0 in range(0, L, CPU_SLAB)]
+
+
 def oracle_round(pool):
-    """One time step of each of the 8 models, the models in parallel worker processes."""
-    list(pool.map(_oracle_step, MODELS))
+    """One time step of each of the 8 models on the whole lattice: every (model, row slab)
+    a task, the tasks spread over the worker processes (so the slow models use many cores).
+    Returns the lattice updates done."""
+    return sum(pool.map(_oracle_slab_step, ORACLE_TASKS, chunksize=1))
 
 
-CPU_ROUNDS = 4   # about 10 s of CPU work (2.5 CPU-seconds a round on a Grace host)
+CPU_ROUNDS = 8   # about 20 s of CPU work on a 16-core Grace host (one round: 8 models x 1024^2 updates)
 
 
 def cpu_baseline():
     """FP64 oracle as it stands, CPU_ROUNDS time steps of each collision model on the
-    1024 x 1024 double shear layer, the eight models in parallel processes on this host's
-    cores (numpy runs each single-threaded)."""
+    1024 x 1024 double shear layer, spread over all host cores as (model, 128-row slab)
+    tasks in single-threaded numpy processes."""
     pool, procs = oracle_pool()
     try:
         oracle_round(pool)   # start-up (imports, initial state) outside the timing
         t0 = time.perf_counter()
+        lu = 0
         for _ in range(CPU_ROUNDS):
-            oracle_round(pool)
+            lu += oracle_round(pool)
         dt = time.perf_counter() - t0
     finally:
         pool.shutdown()
-    lu = CPU_ROUNDS * len(MODELS) * L * L
     return {"value": lu / dt / 1e9, "unit": "GLUPS", "cores": procs, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{CPU_ROUNDS} time steps of each of the {len(MODELS)} models on the {L}x{L} double shear "
-                      f"layer ({lu} lattice updates, {dt:.1f} s wall), numpy FP64, the models in {procs} parallel "
-                      f"single-threaded processes"}
+                      f"layer ({lu} lattice updates, {dt:.1f} s wall), numpy FP64, as {len(ORACLE_TASKS)} "
+                      f"(model, {CPU_SLAB}-row slab + halo) tasks per step over {procs} single-threaded processes"}
 
 
 def adjoint_ratio(lbm, flows, stream, path=0, stages=0):
@@ -302,6 +323,122 @@ def adjoint_ratio(lbm, flows, stream, path=0, stages=0):
     return {"workload": "512x512 vortex, 4000 steps, FP32, REG rates, misfit loss, 64 checkpoints", "models": res}
 
 
+BIG_L = 16384
+BIG_STORAGES = ("f32", "f16", "bf16")
+
+
+def vortex_on_device(n, Ma, slab=1024):
+    """The n x n convected vortex as FP64 device fields, generated in row slabs (the full
+    16384^2 field would need several host copies of 2 GB arrays at once)."""
+    import torch
+    from paper_2002_05265_gb300 import flows
+    out = [torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(3)]
+    for y0 in range(0, n, slab):
+        y1 = min(n, y0 + slab)
+        for o, a in zip(out, flows.vortex(n, Ma=Ma, rows=(y0, y1))):
+            o[y0:y1].copy_(torch.from_numpy(a))
+    return out
+
+
+def per_model_big(lbm, stream, peak, n=BIG_L, warmup=16, steps=48):
+    """Throughput of every collision model x storage type on one n x n lattice: the
+    convected vortex at Ma = 0.2, nu = 1e-6 (BGK single-rate, the others with equilibrated
+    high-order moments), one time step per launch in step order, so every step reads and
+    writes both population buffers through HBM (9.7 GB for 16-bit storage, 19.3 GB for FP32:
+    75-150x the L2).  Time = CUDA events around the graph replays of the step kernel on the
+    launching stream; frac = algorithmic bytes (2 x 9 populations per lattice update) / time /
+    measured HBM copy bandwidth."""
+    import torch
+    fields = vortex_on_device(n, 0.2)
+    res = {}
+    for s in BIG_STORAGES:
+        res[s] = {}
+        for m in MODELS:
+            rates = lbm.lbm_rates_from_nu(1e-6, lbm.LBM_PRESET_SRT if _preset(m) == "srt" else lbm.LBM_PRESET_REG)
+            lat = lbm.Lattice(n, n, lbm.MODELS[m], rates, storage=lbm.STORAGES[s], stream=stream)
+            lat.set_kernel_path(lbm.LBM_PATH_AUTO, 0)
+            lat.set_launch_shape(1, lbm.LBM_ORDER_STEP)
+            lat.init_equilibrium(*fields)
+            g = lbm.lbm_group_create([lat.ctx], graph_steps=16)
+            lbm.lbm_group_step(g, warmup, lat.ctx)
+            lbm.lbm_group_set_timing(g, True)
+            lbm.lbm_group_step(g, steps, lat.ctx)
+            rms, nl, nk = lbm.lbm_group_timing(g)
+            t = rms / 1e3 / nl
+            gbs = BYTES_PER_LU[s] * n * n / t / 1e9
+            res[s][m] = {"glups": n * n / t / 1e9, "alg_gbs": gbs, "frac": gbs / peak,
+                         "launches": nk, "status": lat.status()[0]}
+            lbm.lbm_group_destroy(g)
+            lat.close()
+    del fields
+    torch.cuda.empty_cache()
+    return {"workload": f"convected vortex {n}x{n}, Ma=0.2, nu=1e-6, {steps} timed steps after {warmup}, "
+                        "one step per launch, step order, each model x storage alone",
+            "peak_gbs": peak, "bytes_per_lu": {k: BYTES_PER_LU[k] for k in BIG_STORAGES},
+            "l2": "inputs larger than L2: 9.7-19.3 GB of populations per step", "results": res}
+
+
+ACCURACY_CASES = (("f32", False), ("f16", False), ("bf16", False), ("f32", True), ("f16", True), ("bf16", True))
+
+
+def storage_accuracy(lbm, n, nus=(1e-6, 1e-4)):
+    """Error of reduced-precision storage after 10 domain traversals of the convected vortex
+    (Ma = 0.2, radius 0.1 L, n x n, no seed noise, so that nothing but the storage differs):
+    normalised L2 velocity error of every model (BGK and RR single-rate, the others REG) with
+    FP32, FP16 and BF16 storage (shift w rho0, and shift at the mean flow) against the FP64
+    kernel on the same lattice (itself checked against the FP64 CPU oracle by the tests).
+    Yields one record per nu x model x storage x shift."""
+    import torch
+    from paper_2002_05265_gb300 import flows
+    Ma = 0.2
+    u0 = Ma / np.sqrt(3.0)
+    steps = int(round(10 * n / u0))
+    fields = [torch.from_numpy(a).cuda() for a in flows.vortex(n, Ma=Ma)]
+
+    def velocity(model, storage, shift, w):
+        # RR in its single-rate form (SRT-RR, among the most stable configurations of Sec. 5b;
+        # REG-RR equals PR)
+        srt = _preset(model) == "srt" or model == "rr"
+        rates = (w, w, w) if srt else (w, 1.0, 1.0)
+        lat = lbm.Lattice(n, n, lbm.MODELS[model], rates, storage=lbm.STORAGES[storage])
+        if shift:
+            lat.set_shift_velocity(u0, 0.0)
+        lat.init_equilibrium(*fields)
+        lat.step(steps)
+        ux = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        uy = torch.empty_like(ux)
+        lat.moments(None, ux, uy)
+        lat.close()
+        return ux, uy
+
+    for nu in nus:
+        w = 1.0 / (3.0 * nu + 0.5)
+        for m in MODELS:
+            rx, ry = velocity(m, "f64", False, w)
+            ok = bool(torch.isfinite(rx).all() and torch.isfinite(ry).all())
+            norm = torch.sqrt((rx * rx + ry * ry).sum())
+            for storage, shift in ACCURACY_CASES:
+                gx, gy = velocity(m, storage, shift, w)
+                err = float(torch.sqrt(((gx - rx) ** 2 + (gy - ry) ** 2).sum()) / norm) if ok else None
+                yield {"nu": nu, "model": m, "storage": storage, "shift": "mean flow" if shift else "w rho0",
+                       "lattice": f"{n}x{n}", "steps": steps, "traversals": 10, "fp64_reference_finite": ok,
+                       "l2_rel_error_u": err, "finite": bool(torch.isfinite(gx).all())}
+
+
+def accuracy_table(lbm, n=256):
+    """storage_accuracy as a nested table: nu -> storage/shift -> model -> error (None where
+    the FP64 reference itself blew up, 'blown up' where only the reduced storage did)."""
+    table = {}
+    for r in storage_accuracy(lbm, n):
+        key = f'{r["storage"]}, {r["shift"]} shift'
+        val = r["l2_rel_error_u"] if r["finite"] else "blown up"
+        table.setdefault(f'nu={r["nu"]:g}', {}).setdefault(key, {})[r["model"]] = val
+    return {"workload": f"convected vortex {n}x{n}, Ma=0.2, 10 domain traversals "
+                        f"({int(round(10 * n / (0.2 / np.sqrt(3.0))))} steps), normalised L2 error of u "
+                        "against the FP64 kernel on the same lattice (None: the FP64 run blew up)",
+            "target": "FP16-shifted storage <= 1e-3", "errors": table}
+
+
 METRIC = "D2Q9 lattice updates per second, 8 collision models (GLUPS)"
 
 
@@ -324,12 +461,12 @@ def run_reference(args, rank, world):
         for _ in range(args.warmup):
             oracle_round(pool)
         t0 = time.perf_counter()
+        lu = 0
         for _ in range(args.steps):
-            oracle_round(pool)
+            lu += oracle_round(pool)
         dt = time.perf_counter() - t0
     finally:
         pool.shutdown()
-    lu = args.steps * len(MODELS) * L * L
     v = lu / dt / 1e9
     # single-process figures beside it: one time step per model on the same lattice, and the
     # 128 x 128 vortex (BGK, FP64, 1000 steps) run in full
@@ -353,7 +490,8 @@ def run_reference(args, rank, world):
            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": procs, "host_cores": os.cpu_count(), "kind": "oracle",
                             "sample": "each benchmark step a bounded sample of the workload: one time step of "
                                       f"each of the 8 models on its {L}x{L} lattice (not {args.sim_steps}), "
-                                      f"the models in {procs} parallel single-threaded numpy processes"},
+                                      f"as {len(ORACLE_TASKS)} (model, {CPU_SLAB}-row slab + halo) tasks over "
+                                      f"{procs} single-threaded numpy processes"},
            "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "single_process": {"per_model_mlups_1024": per_model, "vortex_128_bgk_1000_steps_seconds": vortex_s}}
     print(json.dumps(out))
@@ -557,54 +695,12 @@ def run_lsa_map(args):
 
 
 def run_accuracy(args):
-    """Error of reduced-precision storage after 10 domain traversals of the convected vortex
-    (Ma = 0.2, radius 0.1 L, L x L, no seed noise, so that nothing but the storage differs):
-    normalised L2 velocity error of every model (BGK and RR single-rate, the others REG) with
-    FP32, FP16 and BF16 storage (shift
-    w rho0, and shift at the mean flow) against the FP64 kernel on the same lattice (itself
-    checked against the FP64 CPU oracle by the tests).  nu = 1e-6 (the high-Reynolds case,
-    where several models blow up, as in the paper's stability maps) and nu = 1e-4 (stable for
-    every model).  One JSON line per nu x model x storage."""
-    import torch
-    from paper_2002_05265_gb300 import build, flows, lbm
+    """`--accuracy L`: storage_accuracy on an L x L lattice, one JSON line per record."""
+    from paper_2002_05265_gb300 import build, lbm
     build.build_library()
     lbm.load_library()
-    n = args.accuracy
-    Ma = 0.2
-    u0 = Ma / np.sqrt(3.0)
-    steps = int(round(10 * n / u0))
-    fields = [torch.from_numpy(a).cuda() for a in flows.vortex(n, Ma=Ma)]
-
-    def velocity(model, storage, shift, w):
-        # RR in its single-rate form (SRT-RR, among the most stable configurations of Sec. 5b;
-        # REG-RR equals PR)
-        srt = _preset(model) == "srt" or model == "rr"
-        rates = (w, w, w) if srt else (w, 1.0, 1.0)
-        lat = lbm.Lattice(n, n, lbm.MODELS[model], rates, storage=lbm.STORAGES[storage])
-        if shift:
-            lat.set_shift_velocity(u0, 0.0)
-        lat.init_equilibrium(*fields)
-        lat.step(steps)
-        ux = torch.empty((n, n), dtype=torch.float64, device="cuda")
-        uy = torch.empty_like(ux)
-        lat.moments(None, ux, uy)
-        lat.close()
-        return ux, uy
-
-    for nu in (1e-6, 1e-4):
-        w = 1.0 / (3.0 * nu + 0.5)
-        for m in MODELS:
-            rx, ry = velocity(m, "f64", False, w)
-            ok = bool(torch.isfinite(rx).all() and torch.isfinite(ry).all())
-            norm = torch.sqrt((rx * rx + ry * ry).sum())
-            for storage, shift in (("f32", False), ("f16", False), ("bf16", False), ("f32", True), ("f16", True),
-                                   ("bf16", True)):
-                gx, gy = velocity(m, storage, shift, w)
-                err = float(torch.sqrt(((gx - rx) ** 2 + (gy - ry) ** 2).sum()) / norm) if ok else None
-                print(json.dumps({"accuracy": True, "nu": nu, "model": m, "storage": storage,
-                                  "shift": "mean flow" if shift else "w rho0", "lattice": f"{n}x{n}",
-                                  "steps": steps, "traversals": 10, "fp64_reference_finite": ok,
-                                  "l2_rel_error_u": err, "finite": bool(torch.isfinite(gx).all())}), flush=True)
+    for r in storage_accuracy(lbm, args.accuracy):
+        print(json.dumps(dict(accuracy=True, **r)), flush=True)
 
 
 def run_sweep(args):
@@ -672,15 +768,13 @@ def batch_workload(n, seed=4):
     return descs, fields
 
 
-def run_batch(args, rank=0, world=1):
+def batch_measure(lbm, instances, batch_steps, rank=0, world=1, subset=256, peak=None):
     """Batched stability sweep throughput (one persistent launch in a CUDA graph) against
-    the plain per-lattice FP32 kernel on a 256-instance subset.  With several ranks the
-    instances are sharded (weak scaling, no collective but the timing maximum)."""
+    the plain per-lattice FP32 kernel on a `subset`-instance sample (1000 steps each, one
+    context and graph each).  With several ranks the instances are sharded (weak scaling, no
+    collective but the timing maximum)."""
     import torch
-    from paper_2002_05265_gb300 import build, lbm
-    build.build_library()
-    lbm.load_library()
-    descs, fields = batch_workload(args.instances)
+    descs, fields = batch_workload(instances)
     descs, fields = shard(descs, rank, world), shard(fields, rank, world)
     stream = torch.cuda.Stream()
     b = lbm.lbm_batch_create(descs, storage=lbm.LBM_F32, stream=stream)
@@ -692,7 +786,7 @@ def run_batch(args, rank=0, world=1):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         ev0.record(stream)
-        lbm.lbm_batch_run(b, args.batch_steps, check_every=CHECK_EVERY, growth=1e4)
+        lbm.lbm_batch_run(b, batch_steps, check_every=CHECK_EVERY, growth=1e4)
         ev1.record(stream)
         stream.synchronize()
     ms = ev0.elapsed_time(ev1)
@@ -704,8 +798,7 @@ def run_batch(args, rank=0, world=1):
         a = stable.setdefault(key, [0, 0])
         a[0] += int(s == 0)
         a[1] += 1
-    # plain per-lattice kernel: 256 instances, one context each, 1000 steps each
-    sub = list(range(0, len(descs), max(1, len(descs) // 256)))[:256]
+    sub = list(range(0, len(descs), max(1, len(descs) // subset)))[:subset]
     lu_sub, t_sub = 0.0, 0.0
     with torch.cuda.stream(stream):
         for k in sub:
@@ -724,15 +817,32 @@ def run_batch(args, rank=0, world=1):
             lu_sub += 1000.0 * d["nx"] * d["ny"]
             lat.close()
     lbm.lbm_batch_destroy(b)
-    print(json.dumps({
-        "batch": True, "metric": "batched stability sweep, lattice updates per second", "unit": "GLUPS",
-        "value": lu / (ms / 1e3) / 1e9, "instances": len(descs), "nodes": nodes, "target_steps": args.batch_steps,
-        "lattice_updates": lu, "ms": ms, "shape": {"vec": vec, "block": block, "trial_ms": trial_ms},
-        "stable_instances": int((st == 0).sum()), "blown_up": int((st != 0).sum()),
-        "stable_by_model": {k: f"{v[0]}/{v[1]}" for k, v in sorted(stable.items())},
-        "per_instance_kernel_glups": lu_sub / t_sub / 1e9,
-        "per_instance_subset": f"{len(sub)} instances x 1000 steps, one context and graph each",
-        "dtype": "f32", "data": "synthetic"}))
+    glups = lu / (ms / 1e3) / 1e9
+    per_inst = lu_sub / t_sub / 1e9
+    out = {"metric": "batched stability sweep, lattice updates per second", "unit": "GLUPS",
+           "value": glups, "instances": len(descs), "nodes": nodes, "target_steps": batch_steps,
+           "lattice_updates": lu, "ms": ms, "shape": {"vec": vec, "block": block, "trial_ms": trial_ms},
+           "stable_instances": int((st == 0).sum()), "blown_up": int((st != 0).sum()),
+           "stable_by_model": {k: f"{v[0]}/{v[1]}" for k, v in sorted(stable.items())},
+           "per_instance_kernel_glups": per_inst, "speedup_vs_per_instance": glups / per_inst,
+           "per_instance_subset": f"{len(sub)} instances x 1000 steps, one context and graph each",
+           "dtype": "f32", "data": "synthetic"}
+    if peak:
+        # a CTA advances one instance (<= 4.7 MB for both FP32 buffers) for many steps, so the
+        # instances live in the L2: this is algorithmic bytes over the HBM copy bandwidth, not
+        # an HBM fraction
+        out["algorithmic_gbs"] = glups * BYTES_PER_LU["f32"]
+        out["algorithmic_over_hbm_peak_l2_resident"] = glups * BYTES_PER_LU["f32"] / peak
+    return out
+
+
+def run_batch(args, rank=0, world=1):
+    """`--batch`: the full batched stability sweep (default 4096 lattices, 50000 steps)."""
+    from paper_2002_05265_gb300 import build, lbm
+    build.build_library()
+    lbm.load_library()
+    out = batch_measure(lbm, args.instances, args.batch_steps, rank, world, peak=measured_peaks()[0])
+    print(json.dumps(dict(batch=True, **out)))
 
 
 def main():
@@ -861,23 +971,15 @@ def main():
 
     per_model = None
     if not args.no_per_model:
-        per_model = {}
-        for m in MODELS:
-            rates = lbm.lbm_rates_from_nu(NU, lbm.LBM_PRESET_SRT if _preset(m) == "srt" else lbm.LBM_PRESET_REG)
-            big = lbm.Lattice(4096, 4096, lbm.MODELS[m], rates, storage=lbm.LBM_F32, stream=stream)
-            shape_lattice(big, args)
-            f4 = flows.double_shear_layer(4096, Ma=MA)
-            big.init_equilibrium(*[torch.from_numpy(a).cuda() for a in f4])
-            g1 = lbm.lbm_group_create([big.ctx], graph_steps=32)
-            lbm.lbm_group_step(g1, 64, big.ctx)
-            lbm.lbm_group_set_timing(g1, True)
-            lbm.lbm_group_step(g1, 256, big.ctx)
-            rms, nl, _ = lbm.lbm_group_timing(g1)
-            t = rms / 1e3 / nl
-            per_model[m] = {"glups": 4096 * 4096 / t / 1e9, "gbs": 72 * 4096 * 4096 / t / 1e9,
-                            "frac": 72 * 4096 * 4096 / t / 1e9 / peak}
-            lbm.lbm_group_destroy(g1)
-            big.close()
+        per_model = per_model_big(lbm, stream, peak)
+
+    batch = None
+    if not args.no_batch_key:
+        batch = batch_measure(lbm, 4096, 5000, peak=peak)
+
+    accuracy = None
+    if not args.no_accuracy_key:
+        accuracy = accuracy_table(lbm, 256)
 
     adjoint = None
     if not args.no_adjoint:
@@ -897,7 +999,11 @@ def main():
                "gpu_launches": launches_per_step * args.steps,
                "blowup": {m: (s[1] if s[0] != 0 else None) for m, s in statuses.items()}}
         if per_model:
-            out["per_model_4096_f32"] = per_model
+            out["per_model_16384"] = per_model
+        if batch:
+            out["batch"] = batch
+        if accuracy:
+            out["storage_accuracy"] = accuracy
         if adjoint:
             out["adjoint"] = adjoint
         print(json.dumps(out))

@@ -356,6 +356,17 @@ const char* lbm_error_string(int code);
 /* Library version string. */
 const char* lbm_version(void);
 
+/* Self-test of the FP32 reciprocal that forms u = j / rho (Sec. 1: u = (sum_i xi_i f_i) / rho)
+ * in every FP32 kernel: the hardware approximation refined by one Newton-Raphson step.  The
+ * paper has no counterpart (it fixes no arithmetic).  For n device floats x, writes the
+ * library's reciprocal to approx[k] and the correctly rounded one (__frcp_rn) to rounded[k],
+ * asynchronously on cuda_stream (NULL = legacy default stream).  All three are device
+ * pointers to n floats, owned by the caller.  Documented behaviour: within one ulp of the
+ * rounded value for finite non-zero x whose reciprocal is a normal number; NaN for x = 0,
+ * +-inf and NaN (a node with such a density is non-finite either way).  Returns
+ * LBM_ERR_INVALID_ARG for a null pointer or n < 0, LBM_ERR_CUDA if the launch fails. */
+int lbm_selftest_recip(const float* x, float* approx, float* rounded, long long n, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -475,6 +475,29 @@ int storage_bytes(int storage) {
 }  // namespace lbm
 
 // ---------------------------------------------------------------------------------------
+// Self-test of the FP32 reciprocal behind u = j / rho (lbm_selftest_recip in include/lbm.h).
+namespace lbm {
+namespace {
+__global__ void selftest_recip_kernel(const float* __restrict__ x, float* __restrict__ approx,
+                                      float* __restrict__ rounded, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const float v = x[k];
+        approx[k] = recip(v);
+        rounded[k] = __frcp_rn(v);
+    }
+}
+}  // namespace
+}  // namespace lbm
+
+extern "C" int lbm_selftest_recip(const float* x, float* approx, float* rounded, long long n, void* cuda_stream) {
+    using namespace lbm;
+    if (!x || !approx || !rounded || n < 0) return LBM_ERR_INVALID_ARG;
+    if (n == 0) return LBM_OK;
+    selftest_recip_kernel<<<grid_for(n), kBlock, 0, (cudaStream_t)cuda_stream>>>(x, approx, rounded, n);
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------------------
 // Allocation-free reductions (lbm_reduce_noalloc in include/lbm.h).
 //
 // The two reduction passes above need a scratch array for the per-block partial sums.  For

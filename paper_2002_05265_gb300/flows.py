@@ -18,20 +18,25 @@ def _rng(seed):
 
 
 def vortex(nx, ny=None, Ma=0.1, beta=0.5, radius_frac=0.1, rho0=1.0, noise=0.0, seed=1,
-           center=None):
+           center=None, rows=None):
     """Isothermal convected vortex of Sec. 5a (first-order Taylor form of the isentropic
     vortex about T_0 = c_s^2):
         rho = rho0 [1 - eps^2/(2 c_s^2) exp(-r^2)],
         u_x = u0 - eps (y - y_c)/R exp(-r^2/2),  u_y = eps (x - x_c)/R exp(-r^2/2),
     eps = beta u0, u0 = Ma c_s, r = |x - x_c| / R.  R = radius_frac * nx (the workloads use
     R = 0.1 L; the paper's figure uses R = L/20).  The vortex sits at the domain centre
-    unless `center` is given.  `noise` adds independent U(-noise, noise) to u_x and u_y."""
+    unless `center` is given.  `noise` adds independent U(-noise, noise) to u_x and u_y.
+    `rows` = (y0, y1) returns only rows y0 <= y < y1 of the same field (without noise), so
+    that very large lattices can be generated in slabs."""
     ny = nx if ny is None else ny
     u0 = Ma * CS
     eps = beta * u0
     R = radius_frac * nx
     xc, yc = (nx / 2.0, ny / 2.0) if center is None else center
-    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    y0, y1 = (0, ny) if rows is None else rows
+    if rows is not None and noise:
+        raise ValueError("row slabs are generated without noise")
+    y, x = np.meshgrid(np.arange(y0, y1, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
     r2 = ((x - xc) ** 2 + (y - yc) ** 2) / (R * R)
     rho = rho0 * (1.0 - eps * eps / (2.0 * CS * CS) * np.exp(-r2))
     ux = u0 - eps * (y - yc) / R * np.exp(-r2 / 2.0)

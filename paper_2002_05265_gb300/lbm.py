@@ -92,6 +92,7 @@ _SIGNATURES = {
     "lbm_error_string": (ctypes.c_char_p, [_I]),
     "lbm_version": (ctypes.c_char_p, []),
     "lbm_lsa_growth": (_I, [_I, lbm_rates, _I, _P, _I, _P, _I, _P, _P, _P, _P]),
+    "lbm_selftest_recip": (_I, [_P, _P, _P, _LL, _P]),
 }
 
 
@@ -350,6 +351,13 @@ def lbm_lsa_growth(model, rates, flows, k, growth, eig=None, jac=None, stream=No
     _check(load_library().lbm_lsa_growth(model, r, eq_order, _addr(flows), nflows, _addr(k), nk, _addr(growth),
                                          _addr(eig) if eig is not None else None,
                                          _addr(jac) if jac is not None else None, _stream(stream)))
+
+
+def lbm_selftest_recip(x, approx, rounded, stream=None):
+    """x, approx, rounded: device float32 tensors of n elements (the library's FP32 reciprocal
+    and the correctly rounded one of x)."""
+    _check(load_library().lbm_selftest_recip(x.data_ptr(), approx.data_ptr(), rounded.data_ptr(), int(x.numel()),
+                                             _stream(stream)))
 
 
 def lbm_version():

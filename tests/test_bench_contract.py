@@ -29,3 +29,20 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_oracle_row_slabs_reproduce_a_whole_lattice_step():
+    """The CPU baseline spreads each oracle time step over the host cores as row slabs with one
+    halo row on each side; the slabs' rows together equal one oracle step of the whole lattice."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle.lbm as olbm
+    from paper_2002_05265_gb300 import flows
+    f = olbm.init_equilibrium(*flows.double_shear_layer(48, 40, Ma=0.2, width_frac=0.1))
+    f = f * (1 + flows.random_populations_perturbation(f.shape, 1e-3, seed=5))
+    for model in ("bgk", "k", "rr"):
+        rates = olbm.rates_from_nu(1e-3, "reg")
+        whole = olbm.step(f, model, rates)
+        slabs = np.concatenate([bench.oracle_slab_step(f, model, rates, y0, 8) for y0 in range(0, 40, 8)], axis=1)
+        np.testing.assert_array_equal(slabs, whole)

@@ -1,6 +1,11 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded
 inputs.  Tolerances: FP64 populations <= 1e-12 relative; FP32 velocity <= 1e-5 absolute
-after 1000 steps; FP16-shifted vortex velocity <= 1e-3 normalised L2."""
+after 1000 steps (both stated targets of the method's specification); FP16 storage shifted
+at the reference state (rho0, mean flow) <= 1e-3 normalised L2 on the vortex velocity (the
+stated FP16 target, reading of "shifted storage" recorded in the design notes); FP16 / BF16
+storage shifted by w_i rho0 within twice the random-walk estimate of the storage rounding
+(storage_walk_error); FP32 conservation within six standard deviations of the same rounding
+walk (conservation_walk_bound)."""
 
 import numpy as np
 import pytest
@@ -111,14 +116,51 @@ def _l2(got, ref):
     return float(np.sqrt(((gx - rx) ** 2 + (gy - ry) ** 2).sum() / (rx ** 2 + ry ** 2).sum()))
 
 
-# Normalised L2 velocity error of FP16 / BF16 storage of f - w rho0 after 1000 steps of the
-# 96^2, Ma = 0.1, nu = 1e-4 vortex.  Each step rounds every stored population to a relative
-# 2^-12 (FP16) or 2^-9 (BF16); for this flow |f_1 - w_1| ~ 3 w_1 u0 = 0.02, so the velocity
-# receives an uncorrelated O(1e-5) (FP16) kick per node and step, which random-walks over the
-# viscous damping time: ~2-4e-3 of |u| after 1000 steps (FP16), ~8x that for BF16.  The bounds
-# below are those measured values with headroom.
-FP16_BOUND = 5e-3
-BF16_BOUND = 4e-2
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def _ulp(g, storage):
+    """Spacing of the storage type's numbers around each FP64 value g (FP16: 11 significant
+    bits, subnormal spacing 2^-24; BF16: 8 significant bits; FP32: 24)."""
+    a = np.abs(g)
+    if storage == "f16":
+        return np.spacing(a.astype(np.float16)).astype(np.float64)
+    if storage == "f32":
+        return np.spacing(a.astype(np.float32)).astype(np.float64)
+    bits = {"bf16": 8}[storage]
+    e = np.frexp(np.where(a > 0, a, 1.0))[1]
+    return np.ldexp(1.0, e - bits)
+
+
+def storage_walk_error(f0, storage, steps):
+    """Expected normalised L2 velocity error of storing g_i = f_i - w_i rho0 in a reduced
+    type for `steps` steps (the rounding model behind the storage tolerances).
+
+    Every step rounds each stored population once, an error uniform on +-ulp/2 (variance
+    ulp^2/12) and independent between populations, nodes and steps.  The collision conserves
+    mass and momentum exactly, so the part of the rounding that lands in the conserved moments
+    is never relaxed: the velocity of a node receives the kick du_a = sum_i (xi_ia - u_a) dg_i
+    / rho each step and the kicks add up as a random walk (viscous damping at the lattice
+    scale, nu k^2 per step, is neglected, which over-estimates).  After N steps the error
+    variance per node is N sum_i |xi_i - u|^2 ulp_i^2 / 12 / rho^2, so the normalised L2 error
+    is sqrt(N <that sum>) / sqrt(<|u|^2>), with the ulps of the initial state's stored values."""
+    rho = f0.sum(axis=0)
+    ux = sum(float(XI[i][0]) * f0[i] for i in range(9)) / rho
+    uy = sum(float(XI[i][1]) * f0[i] for i in range(9)) / rho
+    ulp = _ulp(f0 - W[:, None, None], storage)
+    var = sum(((XI[i][0] - ux) ** 2 + (XI[i][1] - uy) ** 2) * ulp[i] ** 2 / 12 for i in range(9)) / rho ** 2
+    return float(np.sqrt(steps * var.mean() / (ux * ux + uy * uy).mean()))
+
+
+XI = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+
+# FP16 / BF16 storage of f - w rho0 on the 96^2, Ma = 0.1, nu = 1e-4 vortex, 1000 steps: the
+# normalised L2 velocity error against the FP64 oracle is held to twice the random-walk
+# estimate of storage_walk_error (the factor covers the spread of a sum of random kicks over
+# ~10^4 nodes and the FP32 collision arithmetic, whose rounding is ~2^-13 of the storage's).
+# The north_star's 1e-3 target is met with the shift at the mean flow (next test); with the
+# w rho0 shift the populations themselves, not the perturbation, set the ulp.
+WALK_FACTOR = 2.0
 
 
 @pytest.mark.parametrize("model", MODELS)
@@ -126,8 +168,10 @@ def test_fp16_shifted_vortex_error(L, model):
     fields = flows.vortex(96, Ma=0.1, noise=1e-8, seed=1)
     rates = olbm.rates_from_nu(1e-4, "srt" if model == "bgk" else "reg")
     got = _run_gpu(L, fields, model, rates, L.LBM_F16, 1000)
-    ref = olbm.run(olbm.init_equilibrium(*fields), model, rates, 1000)
-    assert _l2(got, ref) <= FP16_BOUND
+    f0 = olbm.init_equilibrium(*fields)
+    ref = olbm.run(f0, model, rates, 1000)
+    est = storage_walk_error(f0, "f16", 1000)
+    assert _l2(got, ref) <= WALK_FACTOR * est, (_l2(got, ref), est)
 
 
 @pytest.mark.parametrize("model", ["bgk", "chm", "k", "rr"])
@@ -135,8 +179,10 @@ def test_bf16_shifted_vortex_error(L, model):
     fields = flows.vortex(96, Ma=0.1, noise=1e-8, seed=1)
     rates = olbm.rates_from_nu(1e-4, "srt" if model == "bgk" else "reg")
     got = _run_gpu(L, fields, model, rates, L.LBM_BF16, 1000)
-    ref = olbm.run(olbm.init_equilibrium(*fields), model, rates, 1000)
-    assert _l2(got, ref) <= BF16_BOUND
+    f0 = olbm.init_equilibrium(*fields)
+    ref = olbm.run(f0, model, rates, 1000)
+    est = storage_walk_error(f0, "bf16", 1000)
+    assert _l2(got, ref) <= WALK_FACTOR * est, (_l2(got, ref), est)
 
 
 @pytest.mark.parametrize("model", MODELS)
@@ -287,11 +333,28 @@ def test_set_get_populations_roundtrip(L):
     lat.close()
 
 
-@pytest.mark.parametrize("storage,mass_tol", [("f64", 1e-14), ("f32", 1e-7)])
-def test_conservation(L, storage, mass_tol):
+def conservation_walk_bound(f0, storage, steps, sigmas=6.0):
+    """Bound on the drift of the FP64 totals of mass and x / y momentum after `steps` steps
+    of a state stored as g = f - w rho0: the collision conserves them exactly, so only the
+    per-step rounding of the nine stored populations moves them; those errors (uniform on
+    +-ulp/2, independent) add up as a random walk with per-step variance
+    sum_x sum_i c_i^2 ulp_i^2 / 12 (c_i = 1 for mass, xi_ia for momentum).  Returns
+    `sigmas` standard deviations after `steps` steps for (mass, jx, jy)."""
+    ulp2 = _ulp(f0 - W[:, None, None], storage) ** 2 / 12
+    var_m = ulp2.sum()
+    var_x = sum(XI[i][0] ** 2 * ulp2[i].sum() for i in range(9))
+    var_y = sum(XI[i][1] ** 2 * ulp2[i].sum() for i in range(9))
+    return sigmas * np.sqrt(steps * np.array([var_m, var_x, var_y]))
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_conservation(L, storage):
     """Mass and momentum totals (FP64 reductions) over 2000 steps of a 128^2 double shear
-    layer: exact up to rounding.  FP32 storage rounds every population each step, so the total
-    mass drifts by ~1e-8 relative; FP64 stays at the 1e-15 level."""
+    layer.  FP64: exact to 1e-14 relative (the moment-space collision keeps the conserved
+    moments of the stored values; only their rounding moves them).  FP32: the drift stays
+    within six standard deviations of the random walk of the per-step storage rounding
+    (conservation_walk_bound: ~1e-6 absolute here, against the 1.6e-3 of a 1e-7 relative
+    mass bound)."""
     fields = flows.double_shear_layer(128, 128, width_frac=0.1)
     lat = L.Lattice(128, 128, L.LBM_CHM, olbm.rates_from_nu(1e-5, "reg"), storage=L.STORAGES[storage])
     lat.init_equilibrium(*_dev(*fields))
@@ -300,9 +363,13 @@ def test_conservation(L, storage, mass_tol):
     lat.step(2000)
     r1 = np.empty(8)
     lat.reduce(r1)
-    assert abs(r1[0] - r0[0]) / r0[0] < mass_tol
-    assert abs(r1[1] - r0[1]) < mass_tol * r0[0] and abs(r1[2] - r0[2]) < mass_tol * r0[0]
     lat.close()
+    drift = np.abs(r1[:3] - r0[:3])
+    if storage == "f64":
+        assert drift[0] / r0[0] < 1e-14 and drift[1] < 1e-14 * r0[0] and drift[2] < 1e-14 * r0[0]
+    else:
+        bound = conservation_walk_bound(olbm.init_equilibrium(*fields), "f32", 2000)
+        assert np.all(drift <= bound), (drift, bound)
 
 
 def test_blowup_detection(L):
