@@ -26,9 +26,10 @@ Modules
   lsa          collision Jacobian and the discrete eigenproblem (App. A)
   adjoint      reference gradients of a final-state loss (complex step through a run)
 
-Parity status: K (cumulant) is pinned only internally (its definitions are deferred by
-the paper to an external reference); its agreement with the paper's linear-stability
-statements is "parity unpinned".
+Parity status: K (cumulant) is pinned internally and against the paper's simulation
+statements (Sec. 5b; tests/test_oracle_k_readings.py); its agreement with the paper's
+linear-stability statements (Secs. 4b, 4c) is "parity unpinned": no reading of the cumulant
+rebuild reproduces those and the simulations together.
 """
 
 from . import d2q9, moments, equilibrium, collision, lbm, lsa, adjoint  # noqa: F401

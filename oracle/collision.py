@@ -124,16 +124,37 @@ def chm(f, w_nu, w3, w4, eq_order=4):
     return np.array(populations_from_raw(raw_from_hermite(A)))
 
 
-def k(f, w_nu, w3, w4, eq_order=4):
-    """Cumulant model (reading in the module docstring)."""
+def k_reading(f, w_nu, w3, w4, eq_order=4, rebuild="post"):
+    """Cumulant model with a choice of the second-order central moments in the rebuild of
+    K~_22 from the relaxed C_22 (the step the paper defers to an external reference):
+      "post"  K~*_22 = C*_22 + (K~*_20 K~*_02 + 2 K~*_11^2) / rho   (post-collision values;
+              the oracle's reading, `k` below)
+      "pre"   the same with the pre-collision K~_20, K~_02, K~_11
+      "eq"    the same with their equilibrium values (rho c_s^2, rho c_s^2, 0), i.e.
+              K~*_22 = C*_22 + rho c_s^4
+    The alternatives exist to test the reading against the paper's statements about K."""
     if eq_order != 4:
         raise ValueError("the cumulant model is defined with the extended equilibrium")
     rho, ux, uy = macroscopic(f)
-    C = cumulants_from_central(central_moments(f, ux, uy))
-    Ceq = cumulants_from_central(central_moments(feq(rho, ux, uy, 4), ux, uy))
+    K = central_moments(f, ux, uy)
+    C = cumulants_from_central(K)
+    Keq = central_moments(feq(rho, ux, uy, 4), ux, uy)
+    Ceq = cumulants_from_central(Keq)
     Cs = _relax_by_order(C, Ceq, w_nu, w3, w4)
-    Ks = central_from_cumulants(Cs)
+    if rebuild == "post":
+        Ks = central_from_cumulants(Cs)
+    else:
+        src = K if rebuild == "pre" else Keq
+        if rebuild not in ("pre", "eq"):
+            raise ValueError(rebuild)
+        Ks = dict(Cs)
+        Ks[2, 2] = Cs[2, 2] + (src[2, 0] * src[0, 2] + 2.0 * src[1, 1] * src[1, 1]) / rho
     return np.array(populations_from_raw(raw_from_central(Ks, ux, uy)))
+
+
+def k(f, w_nu, w3, w4, eq_order=4):
+    """Cumulant model (reading in the module docstring)."""
+    return k_reading(f, w_nu, w3, w4, eq_order, "post")
 
 
 def rr(f, w_nu, w3, w4, eq_order=4):

@@ -60,10 +60,12 @@ constexpr int kTileConsumerWarps = 8;
 constexpr int kTileThreads = (kTileConsumerWarps + 2) * 32;   // + producer warp + signal warp
 
 // Nodes a consumer thread collides per pass (one vector access per population): 16 bytes
-// for FP64/FP32; for the 16-bit types LBM_TILE_HALF_CV nodes (4 = 8-byte accesses in two
-// passes over a tile, which halves the registers of 8 nodes per pass).
+// for every type.  For the 16-bit types the 8 values of a population stay packed two per
+// 32-bit register and each node converts its own element when it collides, so the pass
+// holds about as many registers as 4 FP32 nodes would; LBM_TILE_HALF_CV = 4 selects the
+// earlier form (8-byte accesses, two passes over a tile, FP32 arrays).
 #ifndef LBM_TILE_HALF_CV
-#define LBM_TILE_HALF_CV 4
+#define LBM_TILE_HALF_CV 8
 #endif
 template <typename S> struct Tile {
     static constexpr int VEC = (sizeof(S) == 2) ? LBM_TILE_HALF_CV : 16 / (int)sizeof(S);
@@ -302,22 +304,109 @@ __device__ __forceinline__ void tile_collide(const unsigned char* stage, S* dstb
     for (int i = 0; i < 9; ++i) vstore<S, VEC>(dst + (long long)i * E.a.plane, out[i]);
 }
 
+// 16-bit storage, 8 nodes per thread: one 16-byte shared-memory load and one 16-byte global
+// store per population; the elements stay packed (two per register) until the node that uses
+// them converts its own one (the pull shift only changes which half it reads).
+template <typename S> struct Half16;
+template <> struct Half16<__half> {
+    __device__ static __forceinline__ float lo(uint32_t u) {
+        __half2 h;
+        memcpy(&h, &u, 4);
+        return __low2float(h);
+    }
+    __device__ static __forceinline__ float hi(uint32_t u) {
+        __half2 h;
+        memcpy(&h, &u, 4);
+        return __high2float(h);
+    }
+    __device__ static __forceinline__ float one(__half s) { return __half2float(s); }
+};
+template <> struct Half16<__nv_bfloat16> {
+    // a bfloat16 is the upper half of the FP32 with the same value
+    __device__ static __forceinline__ float lo(uint32_t u) { return __uint_as_float(u << 16); }
+    __device__ static __forceinline__ float hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+    __device__ static __forceinline__ float one(__nv_bfloat16 s) { return __bfloat162float(s); }
+};
+
+template <int MODEL, int EQ, typename S, bool SHIFT>
+__device__ __forceinline__ void tile_collide_packed(const unsigned char* stage, S* dstbuf, const TileEntry& E,
+                                                    const TilePos& q, int p) {
+    constexpr int VEC = 8;
+    const Consts<float> c = make_consts<float>(E.a);
+    int r = 0, x = p, li = p - 1, ri = p + VEC;
+    if (q.rows > 1 || E.ntx == 0) {
+        r = p / q.w;
+        x = p - r * q.w;
+        if (x == 0) li = p + q.w - 1;
+        if (x + VEC == q.w) ri = p + VEC - q.w;
+    }
+    uint32_t in[9][4];
+    float edge[9];   // the element one node left (xi_x = +1) or right (xi_x = -1) of the 8
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const S* b = reinterpret_cast<const S*>(stage + i * Tile<S>::PLANE + 16);
+        const uint4 v = *reinterpret_cast<const uint4*>(b + p);
+        in[i][0] = v.x; in[i][1] = v.y; in[i][2] = v.z; in[i][3] = v.w;
+        edge[i] = ex_of(i) == 1 ? Half16<S>::one(b[li]) : (ex_of(i) == -1 ? Half16<S>::one(b[ri]) : 0.0f);
+    }
+    uint32_t out[9][4];
+    float prev[9];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) {
+        float gin[9], gout[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int k = j - ex_of(i);   // element of the slot this node pulls, -1 .. 8
+            gin[i] = (k < 0 || k >= VEC) ? edge[i]
+                                         : ((k & 1) ? Half16<S>::hi(in[i][k >> 1]) : Half16<S>::lo(in[i][k >> 1]));
+        }
+        float rho, ux, uy;
+        collide<MODEL, EQ, float, SHIFT>(gin, gout, c, rho, ux, uy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (j & 1) out[i][j >> 1] = pack2(S(), prev[i], gout[i]);
+            else prev[i] = gout[i];
+        }
+    }
+    S* dst = dstbuf + (long long)(q.y + r) * E.a.pitch + q.x0 + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        *reinterpret_cast<uint4*>(dst + (long long)i * E.a.plane) = make_uint4(out[i][0], out[i][1], out[i][2], out[i][3]);
+}
+
 template <typename S, bool SHIFT>
 __device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst, const TileEntry& E, const TilePos& q,
                                              int p) {
-    switch (E.model) {
-        case BGK:
-            if (E.eq_order == 2) tile_collide<BGK, 2, S, SHIFT>(stage, dst, E, q, p);
-            else if (E.eq_order == 3) tile_collide<BGK, 3, S, SHIFT>(stage, dst, E, q, p);
-            else tile_collide<BGK, 4, S, SHIFT>(stage, dst, E, q, p);
-            break;
-        case RM: tile_collide<RM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-        case HM: tile_collide<HM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-        case CM: tile_collide<CM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-        case CHM: tile_collide<CHM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-        case CUM: tile_collide<CUM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-        case PR: tile_collide<PR, 4, S, SHIFT>(stage, dst, E, q, p); break;
-        default: tile_collide<RR, 4, S, SHIFT>(stage, dst, E, q, p); break;
+    if constexpr (sizeof(S) == 2 && Tile<S>::VEC == 8) {
+        switch (E.model) {
+            case BGK:
+                if (E.eq_order == 2) tile_collide_packed<BGK, 2, S, SHIFT>(stage, dst, E, q, p);
+                else if (E.eq_order == 3) tile_collide_packed<BGK, 3, S, SHIFT>(stage, dst, E, q, p);
+                else tile_collide_packed<BGK, 4, S, SHIFT>(stage, dst, E, q, p);
+                break;
+            case RM: tile_collide_packed<RM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            case HM: tile_collide_packed<HM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            case CM: tile_collide_packed<CM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            case CHM: tile_collide_packed<CHM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            case CUM: tile_collide_packed<CUM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            case PR: tile_collide_packed<PR, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            default: tile_collide_packed<RR, 4, S, SHIFT>(stage, dst, E, q, p); break;
+        }
+    } else {
+        switch (E.model) {
+            case BGK:
+                if (E.eq_order == 2) tile_collide<BGK, 2, S, SHIFT>(stage, dst, E, q, p);
+                else if (E.eq_order == 3) tile_collide<BGK, 3, S, SHIFT>(stage, dst, E, q, p);
+                else tile_collide<BGK, 4, S, SHIFT>(stage, dst, E, q, p);
+                break;
+            case RM: tile_collide<RM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            case HM: tile_collide<HM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            case CM: tile_collide<CM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            case CHM: tile_collide<CHM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            case CUM: tile_collide<CUM, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            case PR: tile_collide<PR, 4, S, SHIFT>(stage, dst, E, q, p); break;
+            default: tile_collide<RR, 4, S, SHIFT>(stage, dst, E, q, p); break;
+        }
     }
 }
 

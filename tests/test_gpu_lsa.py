@@ -114,6 +114,23 @@ def test_flow_at_rest_is_linearly_stable(L, model):
     assert np.max(growth) <= 1e-12
 
 
+@pytest.mark.parametrize("preset", ["srt", "reg"])
+def test_cumulant_at_rest_follows_the_post_collision_reading(L, preset):
+    """The library's K model at Ma = 0, nu = 1e-6: no growing mode, as the oracle's reading of
+    the cumulant rebuild (post-collision second-order central moments) predicts -- linearised,
+    it is the CHM collision.  The paper reports K unstable at rest (Sec. 4b); the readings that
+    reproduce that blow every Sec. 5b simulation up (tests/test_oracle_k_readings.py), so this
+    is a statement of the chosen reading, not a parity claim on the paper's linear result."""
+    rates = olbm.rates_from_nu(1e-6, preset)
+    k1 = np.linspace(-np.pi, np.pi, 33)
+    ks = np.array([(a, b) for a in k1 for b in k1])
+    rest = np.array([[1.0, 0.0, 0.0]])
+    growth, _, jk = _gpu(L, "k", rates, rest, ks)
+    assert np.max(growth) <= 1e-12
+    _, _, jc = _gpu(L, "chm", rates, rest, ks)
+    np.testing.assert_allclose(jk, jc, atol=1e-13)
+
+
 def test_srt_moment_models_share_the_bgk_spectrum(L):
     """App. B: with omega_3 = omega_4 = omega_nu, RM, HM, CM and CHM are the BGK collision, so
     their spectra coincide with BGK's for a moving base flow."""

@@ -100,27 +100,10 @@ def test_reversed_streaming_is_caught(monkeypatch):
     _expect_failure(test_vortex_is_carried_downstream)
 
 
-def test_cumulant_reading_matches_the_reported_stability_of_reg_k(monkeypatch):
-    """Reading C-7 of the cumulant back-transform.  Sec. 5b reports REG-K among the most stable
-    models.  With the post-collision second-order central moments in the C22 product terms
-    (the oracle's reading) REG-K at rest (nu = 1e-3) has no growing plane wave; the alternative
-    with pre-collision values grows by a factor e^0.5 per step, which would contradict that
-    report — so the alternative is rejected."""
-    import oracle.lsa as lsa
-    ks = np.linspace(-np.pi, np.pi, 25)
-    rates = lbm.rates_from_nu(1e-3, "reg")
-    G = lsa.collision_map_jacobian("k", 1.0, 0.0, 0.0, rates)
-    assert lsa.max_growth_rate(G, ks, ks) <= 1e-12
-
-    def k_pre(f, w_nu, w3, w4, eq_order=4):
-        rho, ux, uy = collision.macroscopic(f)
-        K = moments.central_moments(f, ux, uy)
-        C = moments.cumulants_from_central(K)
-        Ceq = moments.cumulants_from_central(
-            moments.central_moments(collision.feq(rho, ux, uy, 4), ux, uy))
-        Ks = dict(collision._relax_by_order(C, Ceq, w_nu, w3, w4))
-        Ks[2, 2] = Ks[2, 2] + (K[2, 0] * K[0, 2] + 2.0 * K[1, 1] ** 2) / rho
-        return np.array(moments.populations_from_raw(moments.raw_from_central(Ks, ux, uy)))
-    monkeypatch.setitem(collision.COLLIDE, "k", k_pre)
-    G = lsa.collision_map_jacobian("k", 1.0, 0.0, 0.0, rates)
-    assert lsa.max_growth_rate(G, ks, ks) > 0.1
+def test_pre_collision_cumulant_rebuild_is_caught(monkeypatch):
+    """Planting the pre-collision rebuild of K~_22 (reading "pre" of
+    oracle.collision.k_reading) into the oracle's K makes it grow at rest, which the
+    flow-at-rest pin catches."""
+    from functools import partial
+    monkeypatch.setitem(collision.COLLIDE, "k", partial(collision.k_reading, rebuild="pre"))
+    _expect_failure(td.test_flow_at_rest_is_linearly_stable, "k", "srt")
