@@ -290,13 +290,16 @@ def cpu_baseline():
 
 def adjoint_ratio(lbm, flows, stream, path=0, stages=0):
     """Adjoint / forward time ratio on the 512 x 512 vortex, 4000 steps, FP32, REG rates,
-    misfit loss, sqrt(N) checkpoints: backward (recomputation + adjoint steps) over the plain
-    forward run of the same 4000 steps."""
+    misfit loss to the translated vortex plus N(0, (1e-3 u0)^2) noise, sqrt(N) checkpoints:
+    backward (recomputation + adjoint steps) over the plain forward run of the same 4000
+    steps; then the FP32 gradient against FP64 (adjoint_gradient_check)."""
     import torch
     N, n = 512, 4000
     u0 = 0.1 / np.sqrt(3.0)
     rho, ux, uy = flows.vortex(N, Ma=0.1)
     _, tx, ty = flows.vortex(N, Ma=0.1, center=((N / 2 + u0 * n) % N, N / 2))
+    tx = tx + flows.gaussian_noise(tx.shape, 1e-3 * u0, 21)
+    ty = ty + flows.gaussian_noise(ty.shape, 1e-3 * u0, 22)
     dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (rho, ux, uy, tx, ty)]
     w = 1.0 / (3e-4 + 0.5)
     res = {}
@@ -319,8 +322,56 @@ def adjoint_ratio(lbm, flows, stream, path=0, stages=0):
         loss, gr, (f_ms, b_ms) = lbm.lbm_adjoint_run(lat.ctx, n, 0, dev[3], dev[4], gx, gy, 0)
         lat.close()
         res[m] = {"forward_ms": fwd, "forward_with_checkpoints_ms": f_ms, "backward_ms": b_ms,
-                  "ratio": b_ms / fwd, "loss": loss}
-    return {"workload": "512x512 vortex, 4000 steps, FP32, REG rates, misfit loss, 64 checkpoints", "models": res}
+                  "ratio": b_ms / fwd, "loss": loss,
+                  "gradient_check": adjoint_gradient_check(lbm, flows, m, (w, 1.0, 1.0), n, dev, gx, gy, gr, stream)}
+    return {"workload": "512x512 vortex, 4000 steps, FP32, REG rates, misfit loss to the translated vortex plus "
+                        "N(0, (1e-3 u0)^2) noise, 64 checkpoints", "models": res}
+
+
+def adjoint_gradient_check(lbm, flows, m, rates, n, dev, gx32, gy32, gr32, stream):
+    """FP32 adjoint gradient of the misfit against FP64 adjoint gradients (the FP64 adjoint
+    matches FP64 central differences to 1e-7 in the tests): relative errors of the
+    directional derivative along two smooth random u0 directions and of dL/domega_nu,
+    (a) against the FP64 model's gradient and (b) against the FP64 adjoint on the FP32 run's
+    own final residual (target shifted by u^N_FP32 - u^N_FP64), which isolates the adjoint
+    from the forward trajectory's rounding."""
+    import torch
+    N = dev[0].shape[0]
+
+    def final_u(storage):
+        lat = lbm.Lattice(N, N, lbm.MODELS[m], rates, storage=storage, stream=stream)
+        lat.init_equilibrium(*dev[:3])
+        lat.step(n)
+        mx, my = torch.empty_like(dev[1]), torch.empty_like(dev[2])
+        lat.moments(None, mx, my)
+        lat.synchronize()
+        lat.close()
+        return mx, my
+
+    def adj64(tx, ty):
+        lat = lbm.Lattice(N, N, lbm.MODELS[m], rates, storage=lbm.LBM_F64, stream=stream)
+        lat.init_equilibrium(*dev[:3])
+        gx, gy = torch.empty_like(dev[1]), torch.empty_like(dev[2])
+        _, gr, _ = lbm.lbm_adjoint_run(lat.ctx, n, 0, tx, ty, gx, gy, 0)
+        lat.close()
+        return gx, gy, gr
+
+    u64 = final_u(lbm.LBM_F64)
+    u32 = final_u(lbm.LBM_F32)
+    g64 = adj64(dev[3], dev[4])
+    gsr = adj64((dev[3] - (u32[0] - u64[0])).contiguous(), (dev[4] - (u32[1] - u64[1])).contiguous())
+    dirs = [[torch.from_numpy(flows.smooth_random_field(N, N, 8, 31 + 2 * k + j)).cuda() for j in range(2)]
+            for k in range(2)]
+
+    def rel_errs(ref):
+        out = []
+        for dx, dy in dirs:
+            a = float((gx32 * dx).sum() + (gy32 * dy).sum())
+            b = float((ref[0] * dx).sum() + (ref[1] * dy).sum())
+            out.append(abs(a - b) / abs(b))
+        return {"u0_directional": out, "omega_nu": abs(gr32[0] - ref[2][0]) / abs(ref[2][0])}
+    return {"tolerance": 1e-3, "fp32_vs_fp64": rel_errs(g64), "fp32_vs_fp64_same_residual": rel_errs(gsr),
+            "final_u_fp32_minus_fp64_max": float(torch.max(torch.abs(u32[0] - u64[0])).item())}
 
 
 BIG_L = 16384

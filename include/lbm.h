@@ -174,6 +174,30 @@ int lbm_reduce(lbm_ctx* ctx, double* out8);
 int lbm_reduce_noalloc(const void* populations, int storage, int nx, int ny, int pitch, double rho0,
                        double uref_x, double uref_y, double* out8, void* cuda_stream);
 
+/* Halo exchange of a y-slab decomposition of one periodic lattice over several GPUs.  The
+ * stream step of Eq. StreamCollide (Sec. 4a), f_i(x + xi_i, t + 1) = f*_i(x, t), crosses a
+ * slab boundary only through the three populations with xi_y = +1 (i = 2, 5, 6) going up and
+ * the three with xi_y = -1 (i = 4, 7, 8) going down.  A rank that owns rows y0 .. y1 - 1 of
+ * the global lattice creates a context of ny = (y1 - y0) + 2 rows: local row r holds global
+ * row y0 - 1 + r, and rows 0 and ny - 1 are ghost rows (a copy of the neighbours' boundary rows;
+ * the context's own periodic wrap in y is never used for an owned row).  After every lbm_step
+ * of one step the rank packs, sends, receives and unpacks:
+ *   lbm_halo_pack(ctx, send_up, send_down): send_up <- planes 2, 5, 6 of local row ny - 2 (the
+ *       post-collision populations its last own row emits upwards), send_down <- planes 4, 7, 8
+ *       of local row 1.  Goes to the rank above / below.
+ *   lbm_halo_unpack(ctx, from_below, from_above): from_below (the send_up of the rank below)
+ *       -> planes 2, 5, 6 of ghost row 0; from_above (the send_down of the rank above) ->
+ *       planes 4, 7, 8 of ghost row ny - 1.
+ * Each message is 3 x nx raw storage elements ([3][nx], planes in the order listed, element
+ * type of the context's storage, i.e. 3 * nx * {8, 4, 2} bytes), device pointers owned by the
+ * caller; both calls are asynchronous on the context's stream and copy the stored (shifted)
+ * values bit for bit, so every rank must use the same storage type and shift velocity.  After
+ * an exchange, a step of the slab gives its own rows exactly what a step of the whole lattice
+ * gives them.  The paper has no multi-GPU counterpart.  Errors: LBM_ERR_INVALID_ARG for a null
+ * or host pointer, LBM_ERR_CUDA if the copy kernel fails to launch. */
+int lbm_halo_pack(lbm_ctx* ctx, void* send_up, void* send_down);
+int lbm_halo_unpack(lbm_ctx* ctx, const void* from_below, const void* from_above);
+
 /* Canonical pre-collision populations f^n as FP64 [9][ny][nx] (unshifted), and the inverse
  * (values rounded to the storage type).  Used for checkpoint / resume and tests. */
 int lbm_get_populations(lbm_ctx* ctx, double* f);

@@ -743,6 +743,23 @@ int lbm_moments(lbm_ctx* c, double* rho, double* ux, double* uy, double* pxx, do
     return LBM_OK;
 }
 
+int lbm_halo_pack(lbm_ctx* c, void* send_up, void* send_down) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!send_up || !send_down || !is_device_ptr(send_up) || !is_device_ptr(send_down))
+        return set_err(c, LBM_ERR_INVALID_ARG, "halo messages must be device pointers");
+    LBM_CK(c, lbm::launch_halo(c->storage, c->buf[c->cur], field_args(c), send_up, send_down, true, c->stream));
+    return LBM_OK;
+}
+
+int lbm_halo_unpack(lbm_ctx* c, const void* from_below, const void* from_above) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (!from_below || !from_above || !is_device_ptr(from_below) || !is_device_ptr(from_above))
+        return set_err(c, LBM_ERR_INVALID_ARG, "halo messages must be device pointers");
+    LBM_CK(c, lbm::launch_halo(c->storage, c->buf[c->cur], field_args(c), const_cast<void*>(from_below),
+                               const_cast<void*>(from_above), false, c->stream));
+    return LBM_OK;
+}
+
 int lbm_reduce(lbm_ctx* c, double* out8) {
     if (!c || !out8) return c ? set_err(c, LBM_ERR_INVALID_ARG, "null output") : LBM_ERR_INVALID_ARG;
     const bool dev = is_device_ptr(out8);

@@ -383,6 +383,26 @@ int grid_for(long long n) {
     return (int)g;
 }
 
+// Halo rows of a y-slab.  Messages are [3][nx] elements: `up` holds the planes with xi_y = +1
+// (i = 2, 5, 6) of one row, `down` those with xi_y = -1 (i = 4, 7, 8).  pack: up <- row ny - 2
+// (the slab's last own row), down <- row 1 (its first own row).  unpack: row 0 (the ghost row
+// below) <- up, row ny - 1 (the ghost row above) <- down.  Raw storage elements are copied.
+template <typename E>
+__global__ void halo_kernel(E* buf, FieldArgs a, E* up, E* down, int pack) {
+    const int n = 3 * a.nx;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * n; k += gridDim.x * blockDim.x) {
+        const bool top = k < n;
+        const int j = top ? k : k - n;
+        const int q = j / a.nx, x = j - q * a.nx;
+        const int i = top ? (q == 0 ? 2 : (q == 1 ? 5 : 6)) : (q == 0 ? 4 : (q == 1 ? 7 : 8));
+        E* msg = top ? up : down;
+        const int row = pack ? (top ? a.ny - 2 : 1) : (top ? 0 : a.ny - 1);
+        E* slot = buf + (long long)i * a.plane + (long long)row * a.pitch + x;
+        if (pack) msg[j] = *slot;
+        else *slot = msg[j];
+    }
+}
+
 template <typename S>
 cudaError_t init_t(void* buf, const FieldArgs& a, int eq, const double* r, const double* x, const double* y, cudaStream_t s) {
     init_eq_kernel<S><<<grid_for((long long)a.nx * a.ny), kBlock, 0, s>>>((S*)buf, a, eq, r, x, y);
@@ -452,6 +472,20 @@ cudaError_t launch_gather(int storage, const void* buf, const FieldArgs& a, doub
 cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, double* partials, unsigned* counter,
                           double* out8, int* status, long long* blowup_step, const CheckArgs& c, cudaStream_t s) {
     LBM_DISPATCH(storage, reduce_t<S>(buf, a, partials, counter, out8, status, blowup_step, c, s));
+}
+
+cudaError_t launch_halo(int storage, void* buf, const FieldArgs& a, void* up, void* down, bool pack, cudaStream_t s) {
+    const int grid = grid_for(6LL * a.nx);
+    switch (storage_bytes(storage)) {
+        case 8: halo_kernel<unsigned long long><<<grid, kBlock, 0, s>>>((unsigned long long*)buf, a,
+                                                (unsigned long long*)up, (unsigned long long*)down, pack); break;
+        case 4: halo_kernel<unsigned><<<grid, kBlock, 0, s>>>((unsigned*)buf, a, (unsigned*)up, (unsigned*)down, pack);
+            break;
+        case 2: halo_kernel<unsigned short><<<grid, kBlock, 0, s>>>((unsigned short*)buf, a, (unsigned short*)up,
+                                                                   (unsigned short*)down, pack); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 int storage_vec(int storage) {

@@ -70,6 +70,11 @@ cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, doub
                           double* out8, int* status, long long* blowup_step, const CheckArgs& c,
                           cudaStream_t s);
 
+// Halo rows of a y-slab (lbm_halo_pack / lbm_halo_unpack): messages of [3][nx] raw storage
+// elements; pack reads rows ny - 2 (planes 2, 5, 6 -> up) and 1 (planes 4, 7, 8 -> down), unpack
+// writes up into row 0 (planes 2, 5, 6) and down into row ny - 1 (planes 4, 7, 8).
+cudaError_t launch_halo(int storage, void* buf, const FieldArgs& a, void* up, void* down, bool pack, cudaStream_t s);
+
 // Discrete adjoint (lbm_adjoint.cu).
 struct AdjArgs {
     int nx, ny, pitch, nseg;

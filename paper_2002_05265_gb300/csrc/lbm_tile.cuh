@@ -413,8 +413,12 @@ __device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst,
 // ---- the kernel ------------------------------------------------------------------------------
 // Persistent: CTA b processes tiles b, b + gridDim.x, ...; warp 8 is the producer (one
 // lane issues the copies), warps 0-7 consume.  NS = stages in the ring.
+#ifndef LBM_TILE_HALF_MINB
+#define LBM_TILE_HALF_MINB 2
+#endif
 template <typename S, bool SHIFT, int NS>
-__global__ void __launch_bounds__(kTileThreads, sizeof(S) == 8 ? 1 : 2) tile_step_kernel(const __grid_constant__ TileArgs g) {
+__global__ void __launch_bounds__(kTileThreads, sizeof(S) == 8 ? 1 : (sizeof(S) == 2 ? LBM_TILE_HALF_MINB : 2))
+    tile_step_kernel(const __grid_constant__ TileArgs g) {
     using TS = Tile<S>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * TS::STAGE);

@@ -93,6 +93,8 @@ _SIGNATURES = {
     "lbm_version": (ctypes.c_char_p, []),
     "lbm_lsa_growth": (_I, [_I, lbm_rates, _I, _P, _I, _P, _I, _P, _P, _P, _P]),
     "lbm_selftest_recip": (_I, [_P, _P, _P, _LL, _P]),
+    "lbm_halo_pack": (_I, [_P, _P, _P]),
+    "lbm_halo_unpack": (_I, [_P, _P, _P]),
 }
 
 
@@ -351,6 +353,15 @@ def lbm_lsa_growth(model, rates, flows, k, growth, eig=None, jac=None, stream=No
     _check(load_library().lbm_lsa_growth(model, r, eq_order, _addr(flows), nflows, _addr(k), nk, _addr(growth),
                                          _addr(eig) if eig is not None else None,
                                          _addr(jac) if jac is not None else None, _stream(stream)))
+
+
+def lbm_halo_pack(ctx, send_up, send_down):
+    """send_up / send_down: device tensors of 3 * nx storage elements (any dtype of that size)."""
+    _check(load_library().lbm_halo_pack(ctx, send_up.data_ptr(), send_down.data_ptr()), ctx)
+
+
+def lbm_halo_unpack(ctx, from_below, from_above):
+    _check(load_library().lbm_halo_unpack(ctx, from_below.data_ptr(), from_above.data_ptr()), ctx)
 
 
 def lbm_selftest_recip(x, approx, rounded, stream=None):
