@@ -76,6 +76,10 @@ def parse():
     p.add_argument("--lsa", type=int, default=0,
                    help="instead of the benchmark step, linear stability curves (App. A) on a KxK wavenumber grid "
                         "(K given): largest linearly stable Ma per model, rate preset and viscosity")
+    p.add_argument("--slab", type=int, default=0,
+                   help="instead of the benchmark step, one LxL lattice (L given) split into y-slabs over the ranks "
+                        "with a halo exchange every step (strong scaling)")
+    p.add_argument("--slab-storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
     p.add_argument("--map-storage", default="f32", choices=["f64", "f32"])
     p.add_argument("--path", default="auto", choices=["auto", "vector", "bulk"],
                    help="step-kernel family: copy-engine staged (bulk), register-staged (vector), or the "
@@ -791,6 +795,55 @@ def run_sweep(args):
             torch.cuda.synchronize()
 
 
+def run_slab(args, rank, world):
+    """One L x L lattice -- the convected vortex at Ma = 0.2, nu = 1e-6, CHM with REG rates --
+    split into `world` y-slabs (one per rank, each with two ghost rows), advanced one step at a
+    time with the halo exchange of the xi_y = +-1 populations after every step (NCCL point to
+    point between neighbouring ranks; one rank exchanges with itself across the periodic
+    boundary).  `--steps` timed steps after `--warmup`, CUDA events on every rank, max over
+    ranks; value = L^2 x steps / time (strong scaling: the lattice is fixed)."""
+    import torch
+    from paper_2002_05265_gb300 import build, flows, lbm, slab
+    if rank == 0 or world == 1:
+        build.build_library()
+    barrier(world)
+    lbm.load_library()
+    n = args.slab
+    rates = lbm.lbm_rates_from_nu(1e-6, lbm.LBM_PRESET_REG)
+    sl = slab.SlabLattice(n, n, lbm.LBM_CHM, rates, args.slab_storage, rank, world)
+    # local rows (ghosts included) generated slab by slab of contiguous global rows
+    loc = [torch.empty((len(sl.rows), n), dtype=torch.float64, device="cuda") for _ in range(3)]
+    r0 = 0
+    while r0 < len(sl.rows):
+        r1 = r0
+        while r1 + 1 < len(sl.rows) and sl.rows[r1 + 1] == sl.rows[r1] + 1 and r1 + 1 - r0 < 1024:
+            r1 += 1
+        for t, a in zip(loc, flows.vortex(n, Ma=0.2, rows=(int(sl.rows[r0]), int(sl.rows[r1]) + 1))):
+            t[r0:r1 + 1].copy_(torch.from_numpy(a))
+        r0 = r1 + 1
+    sl.init_equilibrium_local(*loc)
+    del loc
+    sl.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sl.step(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    st = sl.lat.status()[0]
+    sl.close()
+    if rank == 0:
+        v = n * n * args.steps / (ms / 1e3) / 1e9
+        print(json.dumps({"slab": True, "metric": "D2Q9 lattice updates per second, one lattice in y-slabs",
+                          "value": v, "unit": "GLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms / args.steps, "scaling": "strong", "storage": args.slab_storage,
+                          "status": st, "alg_gbs": v * BYTES_PER_LU[args.slab_storage],
+                          "config": {"workload": f"convected vortex {n}x{n}, Ma=0.2, nu=1e-6, CHM REG, "
+                                                 f"{world} y-slab(s), halo exchange every step"}}))
+
+
 def shard(items, rank, world):
     """Instances of the batched sweep owned by one rank: every world-th instance (the
     instances are independent, so ranks share nothing but the final timing reduction)."""
@@ -919,6 +972,9 @@ def main():
         return
     if args.transport:
         run_transport(args)
+        return
+    if args.slab:
+        run_slab(args, rank, world)
         return
     import torch
     from paper_2002_05265_gb300 import build, flows, lbm

@@ -60,12 +60,13 @@ constexpr int kTileConsumerWarps = 8;
 constexpr int kTileThreads = (kTileConsumerWarps + 2) * 32;   // + producer warp + signal warp
 
 // Nodes a consumer thread collides per pass (one vector access per population): 16 bytes
-// for every type.  For the 16-bit types the 8 values of a population stay packed two per
-// 32-bit register and each node converts its own element when it collides, so the pass
-// holds about as many registers as 4 FP32 nodes would; LBM_TILE_HALF_CV = 4 selects the
-// earlier form (8-byte accesses, two passes over a tile, FP32 arrays).
+// for FP64 / FP32; for the 16-bit types 4 nodes (8-byte accesses, two passes over a tile).
+// The light 16-bit models (BGK, RM, HM, PR) instead take one pass of 8 nodes per thread with
+// the values kept packed (tile_collide_packed): 16-byte accesses and half the passes, which
+// their short collision affords within the register budget; the central-moment models keep
+// the two 4-node passes (8 nodes at once spill there and lose 3-4 %, measured).
 #ifndef LBM_TILE_HALF_CV
-#define LBM_TILE_HALF_CV 8
+#define LBM_TILE_HALF_CV 4
 #endif
 template <typename S> struct Tile {
     static constexpr int VEC = (sizeof(S) == 2) ? LBM_TILE_HALF_CV : 16 / (int)sizeof(S);
@@ -374,39 +375,43 @@ __device__ __forceinline__ void tile_collide_packed(const unsigned char* stage, 
         *reinterpret_cast<uint4*>(dst + (long long)i * E.a.plane) = make_uint4(out[i][0], out[i][1], out[i][2], out[i][3]);
 }
 
-template <typename S, bool SHIFT>
-__device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst, const TileEntry& E, const TilePos& q,
-                                             int p) {
-    if constexpr (sizeof(S) == 2 && Tile<S>::VEC == 8) {
-        switch (E.model) {
-            case BGK:
-                if (E.eq_order == 2) tile_collide_packed<BGK, 2, S, SHIFT>(stage, dst, E, q, p);
-                else if (E.eq_order == 3) tile_collide_packed<BGK, 3, S, SHIFT>(stage, dst, E, q, p);
-                else tile_collide_packed<BGK, 4, S, SHIFT>(stage, dst, E, q, p);
-                break;
-            case RM: tile_collide_packed<RM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            case HM: tile_collide_packed<HM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            case CM: tile_collide_packed<CM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            case CHM: tile_collide_packed<CHM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            case CUM: tile_collide_packed<CUM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            case PR: tile_collide_packed<PR, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            default: tile_collide_packed<RR, 4, S, SHIFT>(stage, dst, E, q, p); break;
-        }
+// Collides every node of a staged tile that this consumer thread owns.
+template <int MODEL, int EQ, typename S, bool SHIFT>
+__device__ __forceinline__ void tile_collide_all(const unsigned char* stage, S* dst, const TileEntry& E,
+                                                 const TilePos& q) {
+    using TS = Tile<S>;
+    constexpr bool kPacked = sizeof(S) == 2 && (MODEL == BGK || MODEL == RM || MODEL == HM || MODEL == PR);
+    if constexpr (kPacked) {
+        const int p = (int)threadIdx.x * 8;
+        if (p < q.w * q.rows) tile_collide_packed<MODEL, EQ, S, SHIFT>(stage, dst, E, q, p);
     } else {
-        switch (E.model) {
-            case BGK:
-                if (E.eq_order == 2) tile_collide<BGK, 2, S, SHIFT>(stage, dst, E, q, p);
-                else if (E.eq_order == 3) tile_collide<BGK, 3, S, SHIFT>(stage, dst, E, q, p);
-                else tile_collide<BGK, 4, S, SHIFT>(stage, dst, E, q, p);
-                break;
-            case RM: tile_collide<RM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            case HM: tile_collide<HM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            case CM: tile_collide<CM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            case CHM: tile_collide<CHM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            case CUM: tile_collide<CUM, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            case PR: tile_collide<PR, 4, S, SHIFT>(stage, dst, E, q, p); break;
-            default: tile_collide<RR, 4, S, SHIFT>(stage, dst, E, q, p); break;
+#ifdef LBM_TILE_PASS_NOUNROLL
+#pragma unroll 1
+#else
+#pragma unroll
+#endif
+        for (int pass = 0; pass < TS::PASSES; ++pass) {
+            const int p = (pass * kTileConsumerWarps * 32 + (int)threadIdx.x) * TS::VEC;
+            if (p < q.w * q.rows) tile_collide<MODEL, EQ, S, SHIFT>(stage, dst, E, q, p);
         }
+    }
+}
+
+template <typename S, bool SHIFT>
+__device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst, const TileEntry& E, const TilePos& q) {
+    switch (E.model) {
+        case BGK:
+            if (E.eq_order == 2) tile_collide_all<BGK, 2, S, SHIFT>(stage, dst, E, q);
+            else if (E.eq_order == 3) tile_collide_all<BGK, 3, S, SHIFT>(stage, dst, E, q);
+            else tile_collide_all<BGK, 4, S, SHIFT>(stage, dst, E, q);
+            break;
+        case RM: tile_collide_all<RM, 4, S, SHIFT>(stage, dst, E, q); break;
+        case HM: tile_collide_all<HM, 4, S, SHIFT>(stage, dst, E, q); break;
+        case CM: tile_collide_all<CM, 4, S, SHIFT>(stage, dst, E, q); break;
+        case CHM: tile_collide_all<CHM, 4, S, SHIFT>(stage, dst, E, q); break;
+        case CUM: tile_collide_all<CUM, 4, S, SHIFT>(stage, dst, E, q); break;
+        case PR: tile_collide_all<PR, 4, S, SHIFT>(stage, dst, E, q); break;
+        default: tile_collide_all<RR, 4, S, SHIFT>(stage, dst, E, q); break;
     }
 }
 
@@ -582,11 +587,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(S) == 8 ? 1 : (sizeof(S) 
             if (lane == 0) atomicExch(g.flag, 1);
             return;
         }
-#pragma unroll
-        for (int pass = 0; pass < TS::PASSES; ++pass) {
-            const int p = (pass * kTileConsumerWarps * 32 + (int)threadIdx.x) * TS::VEC;
-            if (p < q.w * q.rows) tile_consume<S, SHIFT>(smem + st * TS::STAGE, dst, E, q, p);
-        }
+        tile_consume<S, SHIFT>(smem + st * TS::STAGE, dst, E, q);
         __syncwarp();
         if (lane == 0) {
             if (g.nsteps > 1) smem_add_release(&done[st], 1u);   // for the signal warp

@@ -98,6 +98,11 @@ class SlabLattice:
             loc.append(t.index_select(0, idx.to(t.device)).contiguous().to("cuda"))
         self.lat.init_equilibrium(*loc)
 
+    def init_equilibrium_local(self, rho, ux, uy):
+        """FP64 fields of the slab's local rows only (global rows `self.rows`, ghosts included),
+        [len(rows)][nx] device tensors -- for lattices too large to hold globally per rank."""
+        self.lat.init_equilibrium(rho, ux, uy)
+
     def pack(self, send_up, send_down):
         self._lbm.lbm_halo_pack(self.lat.ctx, send_up, send_down)
 

@@ -170,15 +170,13 @@ def test_full_size_adjoint_vs_fp64_central_differences(L, model):
     noise = (g.standard_normal(ux.shape), g.standard_normal(uy.shape))
     fd_u = [(loss64(rates, dx, dy, h) - loss64(rates, dx, dy, -h)) / (2 * h) for dx, dy in dirs]
     fd_noise = (loss64(rates, *noise, h) - loss64(rates, *noise, -h)) / (2 * h)
-    # FP64 adjoint against FP64 finite differences: 1e-7.  FP32 rate gradient against FP64
-    # finite differences: 1e-3.  The FP32 u0 gradient follows the FP32 trajectory: the misfit
-    # residual u^N - u* is ~1e-4 while the FP32 trajectory carries rounding that grows to
-    # O(1e-7..1e-6) over 4000 steps, so it departs from the FP64 gradient by ~0.45 % (storage
-    # shifted at the mean flow) to ~1 % (shift w rho0): bounds 1e-2 and 2e-2; and from central
-    # differences of the FP32 model itself (h = 3e-4 along a smooth direction) by ~0.2 %:
-    # bound 5e-3.
-    for storage, shift, tol_w, tol_u in ((L.LBM_F64, None, 1e-7, 1e-7), (L.LBM_F32, (u0, 0.0), 1e-3, 1e-2),
-                                         (L.LBM_F32, None, 1e-3, 2e-2)):
+    # The stated tolerances: FP64 adjoint 1e-7, FP32 adjoint 1e-3 relative against FP64
+    # central differences, for the rate and both u0 directions (with the moment-space collision
+    # the FP32 trajectory's rounding stays ~1e-6 of the misfit residual; the FP32 directional
+    # derivatives agree with the FP64 adjoint's to ~1e-6).  The FP32 model's own central
+    # differences (h = 3e-4 along a smooth direction, truncation ~1e-4 of it) are held to 5e-3.
+    for storage, shift, tol_w, tol_u in ((L.LBM_F64, None, 1e-7, 1e-7), (L.LBM_F32, (u0, 0.0), 1e-3, 1e-3),
+                                         (L.LBM_F32, None, 1e-3, 1e-3)):
         _, gx, gy, gr = _gpu(L, rho, ux, uy, model, rates, storage, n, "misfit", tx, ty, shift=shift)
         assert gr[0] == pytest.approx(fd_w, rel=tol_w)
         for (dx, dy), ref in zip(dirs, fd_u):
@@ -203,50 +201,3 @@ def test_full_size_adjoint_vs_fp64_central_differences(L, model):
             fd32 = (loss32(1.0) - loss32(-1.0)) / (2 * 3e-4)
             got = float((gx * dirs[0][0]).sum() + (gy * dirs[0][1]).sum())
             assert got == pytest.approx(fd32, rel=5e-3)
-
-
-@pytest.mark.parametrize("model", ["chm", "k"])
-def test_fp32_adjoint_meets_1e3_on_the_fp32_residual(L, model):
-    """Where the FP32 u0 gradient's 0.5-1 % gap to the FP64 one comes from: the misfit gradient
-    is J^T r with r = u^N - u*, and the FP32 forward run ends at a u^N that differs from the
-    FP64 one by its accumulated rounding (~1e-6 of u0), about 1 % of the residual (~1e-4).
-    Given the same residual -- the FP64 adjoint run against the target shifted by
-    u^N_FP32 - u^N_FP64, so that it differentiates J_64^T (u^N_FP32 - u*) -- the FP32 adjoint
-    (J_32^T) agrees within the 1e-3 relative tolerance stated for FP32 gradients, along two
-    smooth u0 directions and for the three rate derivatives.  (Same 512 x 512, 4000-step,
-    REG-rate vortex misfit as the finite-difference test, storage shift w rho0.)"""
-    N, n = 512, 4000
-    Ma = 0.1
-    u0 = Ma / np.sqrt(3.0)
-    rho, ux, uy = flows.vortex(N, Ma=Ma, noise=0.0)
-    _, tx, ty = flows.vortex(N, Ma=Ma, center=((N / 2 + u0 * n) % N, N / 2))
-    tx = tx + flows.gaussian_noise(tx.shape, 1e-3 * u0, 21)
-    ty = ty + flows.gaussian_noise(ty.shape, 1e-3 * u0, 22)
-    rates = (1.0 / (3e-4 + 0.5), 1.0, 1.0)
-
-    def final_u(storage):
-        lat = L.Lattice(N, N, L.MODELS[model], rates, storage=storage)
-        lat.init_equilibrium(*[np.ascontiguousarray(a) for a in (rho, ux, uy)])
-        lat.step(n)
-        mx, my = np.empty((N, N)), np.empty((N, N))
-        lat.moments(None, mx, my)
-        lat.close()
-        return mx, my
-
-    u64x, u64y = final_u(L.LBM_F64)
-    u32x, u32y = final_u(L.LBM_F32)
-    _, g32x, g32y, gr32 = _gpu(L, rho, ux, uy, model, rates, L.LBM_F32, n, "misfit", tx, ty)
-    _, gsx, gsy, grs = _gpu(L, rho, ux, uy, model, rates, L.LBM_F64, n, "misfit",
-                            tx - (u32x - u64x), ty - (u32y - u64y))
-    _, g64x, g64y, gr64 = _gpu(L, rho, ux, uy, model, rates, L.LBM_F64, n, "misfit", tx, ty)
-    dirs = [(flows.smooth_random_field(N, N, 8, 31 + 2 * k), flows.smooth_random_field(N, N, 8, 32 + 2 * k))
-            for k in range(2)]
-    for dx, dy in dirs:
-        d32 = float((g32x * dx).sum() + (g32y * dy).sum())
-        ds = float((gsx * dx).sum() + (gsy * dy).sum())
-        d64 = float((g64x * dx).sum() + (g64y * dy).sum())
-        assert d32 == pytest.approx(ds, rel=1e-3)
-        # ... while the plain FP64 gradient, on its own residual, is measurably further away
-        assert abs(d32 - d64) > abs(d32 - ds)
-    assert gr32[0] == pytest.approx(grs[0], rel=1e-3)
-    assert np.max(np.abs(gr32 - grs)) <= 1e-3 * np.max(np.abs(grs))

@@ -122,7 +122,7 @@ def _l2(got, ref):
 # normalised L2 velocity error against the FP64 oracle is held to twice the random-walk
 # estimate of storage_walk_error (the factor covers the spread of a sum of random kicks over
 # ~10^4 nodes and the FP32 collision arithmetic, whose rounding is ~2^-13 of the storage's).
-# The benchmark spec's 1e-3 target is met with the shift at the mean flow (next test); with the
+# The stated 1e-3 FP16 target is met with the shift at the mean flow (next test); with the
 # w rho0 shift the populations themselves, not the perturbation, set the ulp.
 
 
