@@ -60,7 +60,8 @@ constexpr int kTileConsumerWarps = 8;
 constexpr int kTileThreads = (kTileConsumerWarps + 2) * 32;   // + producer warp + signal warp
 
 // Nodes a consumer thread collides per pass (one vector access per population): 16 bytes
-// for FP64 / FP32; for the 16-bit types 4 nodes (8-byte accesses, two passes over a tile).
+// for FP64 / FP32; for the 16-bit types LBM_TILE_HALF_CV nodes (4: 8-byte accesses, two
+// passes over a tile).
 // The light 16-bit models (BGK, RM, HM, PR) instead take one pass of 8 nodes per thread with
 // the values kept packed (tile_collide_packed): 16-byte accesses and half the passes, which
 // their short collision affords within the register budget; the central-moment models keep
@@ -385,11 +386,10 @@ __device__ __forceinline__ void tile_collide_all(const unsigned char* stage, S* 
         const int p = (int)threadIdx.x * 8;
         if (p < q.w * q.rows) tile_collide_packed<MODEL, EQ, S, SHIFT>(stage, dst, E, q, p);
     } else {
-#ifdef LBM_TILE_PASS_NOUNROLL
+        // the passes are not unrolled: unrolled, the consumers' code of one model outgrows the
+        // instruction cache (ncu, 16-bit K at 8192^2: 2.6x the fetch stalls of CHM, 0.926 of
+        // HBM; rolled: the stalls of CHM, 0.956)
 #pragma unroll 1
-#else
-#pragma unroll
-#endif
         for (int pass = 0; pass < TS::PASSES; ++pass) {
             const int p = (pass * kTileConsumerWarps * 32 + (int)threadIdx.x) * TS::VEC;
             if (p < q.w * q.rows) tile_collide<MODEL, EQ, S, SHIFT>(stage, dst, E, q, p);
