@@ -178,14 +178,22 @@ const void* pick_group_kernel(int storage, bool shifted) {
 // rows of a whole number of 16-byte chunks: every bulk copy of the tile kernel is aligned
 bool row_aligned(const lbm_ctx* c) { return ((long long)c->nx * lbm::storage_bytes(c->storage)) % 16 == 0; }
 
-const void* pick_tile_kernel(int storage, bool shifted, int stages) {
+const void* pick_tile_kernel(int storage, bool shifted, int stages, bool light) {
     switch (storage) {
-        case LBM_F64: return lbm::tile_kernel_f64(shifted, stages);
-        case LBM_F32: return lbm::tile_kernel_f32(shifted, stages);
-        case LBM_F16: return lbm::tile_kernel_f16(shifted, stages);
-        case LBM_BF16: return lbm::tile_kernel_bf16(shifted, stages);
+        case LBM_F64: return lbm::tile_kernel_f64(shifted, stages, light);
+        case LBM_F32: return lbm::tile_kernel_f32(shifted, stages, light);
+        case LBM_F16: return lbm::tile_kernel_f16(shifted, stages, light);
+        case LBM_BF16: return lbm::tile_kernel_bf16(shifted, stages, light);
         default: return nullptr;
     }
+}
+// the light 16-bit kernel form serves groups whose lattices all run BGK, RM, HM or PR
+bool light_models(lbm_ctx* const* ctxs, int n) {
+    for (int k = 0; k < n; ++k) {
+        const int m = ctxs[k]->model;
+        if (m != LBM_BGK && m != LBM_RM && m != LBM_HM && m != LBM_PR) return false;
+    }
+    return true;
 }
 int tile_width(int storage) {
     switch (storage) {
@@ -892,7 +900,7 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         for (int sh = 0; sh < 2 && tile; ++sh) {
-            const void* k = pick_tile_kernel(storage, sh == 1, stages);
+            const void* k = pick_tile_kernel(storage, sh == 1, stages, light_models(ctxs, n));
             int per_sm = 0;
             if (!k || cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, g->tsmem) != cudaSuccess ||
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, lbm::kTileThreads, g->tsmem) != cudaSuccess ||

@@ -19,12 +19,14 @@ const void* group_kernel_f32(bool shifted);
 const void* group_kernel_f16(bool shifted);
 const void* group_kernel_bf16(bool shifted);
 
-// Bulk-copy staged step kernel (tile_step_kernel<S, shifted, stages>, one TileArgs parameter,
-// kTileThreads threads, tile_smem_bytes dynamic shared memory) per storage; stages 2-4.
-const void* tile_kernel_f64(bool shifted, int stages);
-const void* tile_kernel_f32(bool shifted, int stages);
-const void* tile_kernel_f16(bool shifted, int stages);
-const void* tile_kernel_bf16(bool shifted, int stages);
+// Bulk-copy staged step kernel (tile_step_kernel<S, shifted, stages, form>, one TileArgs
+// parameter, kTileThreads threads, tile_smem_bytes dynamic shared memory) per storage; stages
+// 2-4; `light` selects the 16-bit form for launches whose lattices all run BGK, RM, HM or PR
+// (ignored for FP64 / FP32).
+const void* tile_kernel_f64(bool shifted, int stages, bool light);
+const void* tile_kernel_f32(bool shifted, int stages, bool light);
+const void* tile_kernel_f16(bool shifted, int stages, bool light);
+const void* tile_kernel_bf16(bool shifted, int stages, bool light);
 
 // Batched persistent sweep kernel for (vector width, CTA size); nullptr if not instantiated.
 const void* batch_kernel_f64(int vec, int block);

@@ -62,10 +62,13 @@ constexpr int kTileThreads = (kTileConsumerWarps + 2) * 32;   // + producer warp
 // Nodes a consumer thread collides per pass (one vector access per population): 16 bytes
 // for FP64 / FP32; for the 16-bit types LBM_TILE_HALF_CV nodes (4: 8-byte accesses, two
 // passes over a tile).
-// The light 16-bit models (BGK, RM, HM, PR) instead take one pass of 8 nodes per thread with
-// the values kept packed (tile_collide_packed): 16-byte accesses and half the passes, which
-// their short collision affords within the register budget; the central-moment models keep
-// the two 4-node passes (8 nodes at once spill there and lose 3-4 %, measured).
+// 16-bit storage has two forms of the kernel.  The general form (every model) takes the two
+// 4-node passes.  The light form (FORM = 1), used when every lattice of a launch runs BGK, RM,
+// HM or PR, instead takes one pass of 8 nodes per thread with the values kept packed
+// (tile_collide_packed): 16-byte accesses and half the passes, which their short collision
+// affords.  They are separate kernels because the packed path's register pressure makes the
+// compiler spill in the loop every model shares (measured: the central-moment models then lose
+// 2-4 %, and with 8 nodes at once themselves 3-6 %).
 #ifndef LBM_TILE_HALF_CV
 #define LBM_TILE_HALF_CV 4
 #endif
@@ -377,12 +380,11 @@ __device__ __forceinline__ void tile_collide_packed(const unsigned char* stage, 
 }
 
 // Collides every node of a staged tile that this consumer thread owns.
-template <int MODEL, int EQ, typename S, bool SHIFT>
+template <int MODEL, int EQ, typename S, bool SHIFT, bool PACKED>
 __device__ __forceinline__ void tile_collide_all(const unsigned char* stage, S* dst, const TileEntry& E,
                                                  const TilePos& q) {
     using TS = Tile<S>;
-    constexpr bool kPacked = sizeof(S) == 2 && (MODEL == BGK || MODEL == RM || MODEL == HM || MODEL == PR);
-    if constexpr (kPacked) {
+    if constexpr (PACKED && sizeof(S) == 2) {
         const int p = (int)threadIdx.x * 8;
         if (p < q.w * q.rows) tile_collide_packed<MODEL, EQ, S, SHIFT>(stage, dst, E, q, p);
     } else {
@@ -397,33 +399,44 @@ __device__ __forceinline__ void tile_collide_all(const unsigned char* stage, S* 
     }
 }
 
-template <typename S, bool SHIFT>
+template <typename S, bool SHIFT, int FORM>
 __device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst, const TileEntry& E, const TilePos& q) {
+    if constexpr (FORM == 1) {
+        // light form: only the models it is launched for
+        switch (E.model) {
+            case BGK:
+                if (E.eq_order == 2) tile_collide_all<BGK, 2, S, SHIFT, true>(stage, dst, E, q);
+                else if (E.eq_order == 3) tile_collide_all<BGK, 3, S, SHIFT, true>(stage, dst, E, q);
+                else tile_collide_all<BGK, 4, S, SHIFT, true>(stage, dst, E, q);
+                break;
+            case RM: tile_collide_all<RM, 4, S, SHIFT, true>(stage, dst, E, q); break;
+            case HM: tile_collide_all<HM, 4, S, SHIFT, true>(stage, dst, E, q); break;
+            default: tile_collide_all<PR, 4, S, SHIFT, true>(stage, dst, E, q); break;
+        }
+        return;
+    }
     switch (E.model) {
         case BGK:
-            if (E.eq_order == 2) tile_collide_all<BGK, 2, S, SHIFT>(stage, dst, E, q);
-            else if (E.eq_order == 3) tile_collide_all<BGK, 3, S, SHIFT>(stage, dst, E, q);
-            else tile_collide_all<BGK, 4, S, SHIFT>(stage, dst, E, q);
+            if (E.eq_order == 2) tile_collide_all<BGK, 2, S, SHIFT, false>(stage, dst, E, q);
+            else if (E.eq_order == 3) tile_collide_all<BGK, 3, S, SHIFT, false>(stage, dst, E, q);
+            else tile_collide_all<BGK, 4, S, SHIFT, false>(stage, dst, E, q);
             break;
-        case RM: tile_collide_all<RM, 4, S, SHIFT>(stage, dst, E, q); break;
-        case HM: tile_collide_all<HM, 4, S, SHIFT>(stage, dst, E, q); break;
-        case CM: tile_collide_all<CM, 4, S, SHIFT>(stage, dst, E, q); break;
-        case CHM: tile_collide_all<CHM, 4, S, SHIFT>(stage, dst, E, q); break;
-        case CUM: tile_collide_all<CUM, 4, S, SHIFT>(stage, dst, E, q); break;
-        case PR: tile_collide_all<PR, 4, S, SHIFT>(stage, dst, E, q); break;
-        default: tile_collide_all<RR, 4, S, SHIFT>(stage, dst, E, q); break;
+        case RM: tile_collide_all<RM, 4, S, SHIFT, false>(stage, dst, E, q); break;
+        case HM: tile_collide_all<HM, 4, S, SHIFT, false>(stage, dst, E, q); break;
+        case CM: tile_collide_all<CM, 4, S, SHIFT, false>(stage, dst, E, q); break;
+        case CHM: tile_collide_all<CHM, 4, S, SHIFT, false>(stage, dst, E, q); break;
+        case CUM: tile_collide_all<CUM, 4, S, SHIFT, false>(stage, dst, E, q); break;
+        case PR: tile_collide_all<PR, 4, S, SHIFT, false>(stage, dst, E, q); break;
+        default: tile_collide_all<RR, 4, S, SHIFT, false>(stage, dst, E, q); break;
     }
 }
 
 // ---- the kernel ------------------------------------------------------------------------------
 // Persistent: CTA b processes tiles b, b + gridDim.x, ...; warp 8 is the producer (one
-// lane issues the copies), warps 0-7 consume.  NS = stages in the ring.
-#ifndef LBM_TILE_HALF_MINB
-#define LBM_TILE_HALF_MINB 2
-#endif
-template <typename S, bool SHIFT, int NS>
-__global__ void __launch_bounds__(kTileThreads, sizeof(S) == 8 ? 1 : (sizeof(S) == 2 ? LBM_TILE_HALF_MINB : 2))
-    tile_step_kernel(const __grid_constant__ TileArgs g) {
+// lane issues the copies), warps 0-7 consume.  NS = stages in the ring; FORM = 0 general,
+// 1 the light 16-bit form (BGK, RM, HM, PR only).
+template <typename S, bool SHIFT, int NS, int FORM>
+__global__ void __launch_bounds__(kTileThreads, sizeof(S) == 8 ? 1 : 2) tile_step_kernel(const __grid_constant__ TileArgs g) {
     using TS = Tile<S>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * TS::STAGE);
@@ -587,7 +600,7 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(S) == 8 ? 1 : (sizeof(S) 
             if (lane == 0) atomicExch(g.flag, 1);
             return;
         }
-        tile_consume<S, SHIFT>(smem + st * TS::STAGE, dst, E, q);
+        tile_consume<S, SHIFT, FORM>(smem + st * TS::STAGE, dst, E, q);
         __syncwarp();
         if (lane == 0) {
             if (g.nsteps > 1) smem_add_release(&done[st], 1u);   // for the signal warp

@@ -3,5 +3,5 @@
 #include "lbm_internal.h"
 
 namespace lbm {
-const void* tile_kernel_f32(bool shifted, int stages) { return tile_kernel_table<float>(shifted, stages); }
+const void* tile_kernel_f32(bool shifted, int stages, bool) { return tile_kernel_table<float, 0>(shifted, stages); }
 }  // namespace lbm
