@@ -552,7 +552,9 @@ def run_reference(args, rank, world):
     print(json.dumps(out))
 
 
-MAP_CONFIGS = [("bgk", "srt")] + [(m, c) for m in ("rm", "hm", "cm", "chm", "k", "rr") for c in ("srt", "reg")]
+MAP_CONFIGS = ([("bgk", "srt")] + [(m, c) for m in ("rm", "hm", "cm", "chm", "k", "rr") for c in ("srt", "reg")]
+               # the two alternative readings of the cumulant rebuild (pre-collision / equilibrium)
+               + [(m, c) for m in ("k_pre", "k_eq") for c in ("srt", "reg")])
 
 
 def run_stability_map(args):

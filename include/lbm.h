@@ -44,7 +44,15 @@ typedef enum {
     LBM_CHM = 4,   /* central Hermite moments  (Eqs. CHpoly, CHMcoll, CHM2HM_Q9)            */
     LBM_K   = 5,   /* cumulants; C22 = K22 - (K20 K02 + 2 K11^2)/rho        (Sec. 4c)       */
     LBM_PR  = 6,   /* standard regularized (= REG-HM)                       (Sec. 5c)       */
-    LBM_RR  = 7    /* recursive regularized      (Eqs. HMColl_Q9, RRformulas_D2Q9)          */
+    LBM_RR  = 7,   /* recursive regularized      (Eqs. HMColl_Q9, RRformulas_D2Q9)          */
+    /* Two further readings of the cumulant model, whose definition the paper defers to an
+     * external reference: the fourth-order central moment is rebuilt from the relaxed C22
+     * with the product term of the PRE-collision second-order central moments (LBM_K_PRE) or
+     * of their EQUILIBRIUM values (LBM_K_EQ), instead of the post-collision ones of LBM_K.
+     * Linearly unstable at rest (Sec. 4b reports K so), but every simulation of Sec. 5b with
+     * them blows up; kept to study that statement.  Same kernels as LBM_K. */
+    LBM_K_PRE = 8,
+    LBM_K_EQ  = 9
 } lbm_model;
 
 /* Population storage.  Every storage type holds the shifted populations

@@ -188,7 +188,10 @@ def pr(f, w_nu, w3=None, w4=None, eq_order=4):
     return hm(f, w_nu, 1.0, 1.0, eq_order)
 
 
-COLLIDE = {"bgk": bgk, "rm": rm, "hm": hm, "cm": cm, "chm": chm, "k": k, "pr": pr, "rr": rr}
+COLLIDE = {"bgk": bgk, "rm": rm, "hm": hm, "cm": cm, "chm": chm, "k": k, "pr": pr, "rr": rr,
+           # the two alternative readings of the cumulant rebuild (see k_reading)
+           "k_pre": lambda f, w_nu, w3, w4, eq_order=4: k_reading(f, w_nu, w3, w4, eq_order, "pre"),
+           "k_eq": lambda f, w_nu, w3, w4, eq_order=4: k_reading(f, w_nu, w3, w4, eq_order, "eq")}
 
 
 def collide(model, f, w_nu, w3, w4, eq_order=4):

@@ -69,6 +69,7 @@ __device__ __forceinline__ void adjoint_body(const S* __restrict__ state, const 
     VjpConsts<T> vc;
     vc.w = ct[0]; vc.w3 = ct[1]; vc.w4 = ct[2]; vc.rho0 = ct[3]; vc.urx = ct[4]; vc.ury = ct[5];
     vc.Xr = ct[12]; vc.Yr = ct[13];
+    vc.kap = ct[16]; vc.kapw = ct[17];
     // per-thread sums in the collision precision (a thread handles a few nodes), FP64 from
     // the block fold on
     T acc[3] = {T(0), T(0), T(0)};
@@ -273,8 +274,9 @@ const void* adjoint_kernel_for(int model) {
 
 }  // namespace
 
-int adjoint_plan(int storage, int model, int nx, int ny, int pitch, long long plane, double w, double w3, double w4,
-                 double rho0, double urx, double ury, AdjointPlan* p) {
+int adjoint_plan(int storage, int model, int kread, int nx, int ny, int pitch, long long plane, double w, double w3,
+                 double w4, double rho0, double urx, double ury, AdjointPlan* p) {
+    static_assert(kNumConsts <= (int)(sizeof(AdjArgs::cf) / sizeof(float)), "AdjArgs constant table too small");
     if (storage != LBM_F64 && storage != LBM_F32) return LBM_ERR_UNSUPPORTED;
     const int vec = storage_vec(storage);
     p->storage = storage;
@@ -282,7 +284,7 @@ int adjoint_plan(int storage, int model, int nx, int ny, int pitch, long long pl
     p->a.w_nu = w; p->a.w3 = w3; p->a.w4 = w4; p->a.rho0 = rho0; p->a.urx = urx; p->a.ury = ury;
     {
         StepArgs t{};
-        t.w_nu = w; t.w3 = w3; t.w4 = w4; t.rho0 = rho0; t.urx = urx; t.ury = ury;
+        t.w_nu = w; t.w3 = w3; t.w4 = w4; t.rho0 = rho0; t.urx = urx; t.ury = ury; t.kread = kread;
         fill_consts(t);
         for (int k = 0; k < kNumConsts; ++k) { p->a.cd[k] = t.cd[k]; p->a.cf[k] = t.cf[k]; }
     }

@@ -21,6 +21,7 @@ namespace lbm {
 // Collision constants of the reverse pass (from the host-filled table of StepArgs / AdjArgs).
 template <typename T> struct VjpConsts {
     T w, w3, w4, rho0, urx, ury, Xr, Yr;   // rates, shift density and velocity, mu_2(u_ref)
+    T kap, kapw;                           // cumulant rebuild: kappa and dkappa/dw (kNumConsts)
 };
 
 template <int MODEL, typename T>
@@ -137,9 +138,10 @@ __device__ __forceinline__ void collide_vjp(const T (&g)[9], const T (&v)[9], T 
             db02 += cs2 * db22;
         } else {
             // d22 = k22 - K22*, K22* = c4 C22 + cs2 (K20 + K02) + (K20 K02 + 2 K11^2) / rho,
-            // C22 = k22 - cs2 (n20 + n02) - (n20 n02 + 2 n11^2) / rho, K = (1 - w) n (order 2)
-            const T c2 = T(1) - w, c4 = T(1) - w4;
-            const T K20 = c2 * n20, K02 = c2 * n02, K11 = c2 * n11;
+            // C22 = k22 - cs2 (n20 + n02) - (n20 n02 + 2 n11^2) / rho, K = kappa n (order 2):
+            // kappa = 1 - w for the post-collision rebuild, 1 or 0 for the other readings
+            const T kap = c.kap, c4 = T(1) - w4;
+            const T K20 = kap * n20, K02 = kap * n02, K11 = kap * n11;
             const T C22 = k22 - cs2 * (n20 + n02) - (n20 * n02 + T(2) * n11 * n11) * irho;
             const T Kb = -db22;                       // adjoint of K22*
             const T Cb = c4 * Kb;                     // adjoint of C22
@@ -147,10 +149,10 @@ __device__ __forceinline__ void collide_vjp(const T (&g)[9], const T (&v)[9], T 
             const T Kb20 = Kb * (cs2 + K02 * irho), Kb02 = Kb * (cs2 + K20 * irho), Kb11 = Kb * (T(4) * K11 * irho);
             irhob = Kb * (K20 * K02 + T(2) * K11 * K11) - Cb * (n20 * n02 + T(2) * n11 * n11);
             kb22 = db22 + Cb;
-            xb20 = c2 * Kb20 - Cb * (cs2 + n02 * irho);
-            xb02 = c2 * Kb02 - Cb * (cs2 + n20 * irho);
-            xb11 = c2 * Kb11 - Cb * (T(4) * n11 * irho);
-            wb = -((Kb20 * n20 + Kb02 * n02) + Kb11 * n11);
+            xb20 = kap * Kb20 - Cb * (cs2 + n02 * irho);
+            xb02 = kap * Kb02 - Cb * (cs2 + n20 * irho);
+            xb11 = kap * Kb11 - Cb * (T(4) * n11 * irho);
+            wb = c.kapw * ((Kb20 * n20 + Kb02 * n02) + Kb11 * n11);
         }
         // u enters S(u): D21 = d21 + 2 ux d11 + uy d20, D12 = d12 + 2 uy d11 + ux d02,
         // D22 = d22 + 2 ux d12 + 2 uy d21 + ux^2 d02 + uy^2 d20 + 4 ux uy d11

@@ -107,6 +107,10 @@ int set_err(lbm_ctx* c, int code, const char* fmt, ...) {
 
 bool rate_ok(double w) { return std::isfinite(w) && w > 0.0 && w < 2.0; }
 
+// The cumulant readings LBM_K_PRE / LBM_K_EQ run the kernels of LBM_K with other constants.
+int kernel_model(int model) { return (model == LBM_K_PRE || model == LBM_K_EQ) ? LBM_K : model; }
+int cumulant_read(int model) { return model == LBM_K_PRE ? 1 : (model == LBM_K_EQ ? 2 : 0); }
+
 bool rates_ok(const lbm_rates& r) { return rate_ok(r.omega_nu) && rate_ok(r.omega3) && rate_ok(r.omega4); }
 
 const void* pick_kernel(int storage, int model, int eq_order, bool shifted) {
@@ -137,7 +141,7 @@ int resident_grid(const void* kernel, int block, long long work_threads) {
 }
 
 int select_kernel(lbm_ctx* c) {
-    const void* k = pick_kernel(c->storage, c->model, c->eq_order, is_shifted(c));
+    const void* k = pick_kernel(c->storage, kernel_model(c->model), c->eq_order, is_shifted(c));
     if (!k) return set_err(c, LBM_ERR_UNSUPPORTED, "no kernel for this configuration");
     c->kernel = k;
     const long long work = ((long long)c->ny * c->nseg + 31) / 32 * 32;
@@ -154,6 +158,7 @@ StepArgs step_args(const lbm_ctx* c) {
     a.rho0 = c->rho0;
     a.urx = c->urx;
     a.ury = c->ury;
+    a.kread = cumulant_read(c->model);
     lbm::fill_consts(a);
     return a;
 }
@@ -265,7 +270,7 @@ int launch_group_once(lbm_group* g, cudaStream_t s, int sh) {
         e.src = c->buf[c->cur];
         e.dst = c->buf[c->cur ^ 1];
         e.a = step_args(c);
-        e.model = c->model;
+        e.model = kernel_model(c->model);
         e.eq_order = c->eq_order;
         e.begin = g->begin[k];
         e.total = (unsigned)c->ny * (unsigned)c->nseg;
@@ -311,7 +316,7 @@ cudaError_t launch_tile(lbm_group* g, const void* const* buf0, void* const* buf1
         e.ring = ring;
         e.cbase = g->cbase[k];
         e.a = step_args(c);
-        e.model = c->model;
+        e.model = kernel_model(c->model);
         e.eq_order = c->eq_order;
         e.rows = tile_rows(c, W);
         e.ntx = e.rows > 1 ? 0 : (c->nx + W - 1) / W;
@@ -570,7 +575,7 @@ int lbm_create(lbm_ctx** out, int nx, int ny, int periodic, int model, lbm_rates
     if (!out) return LBM_ERR_INVALID_ARG;
     *out = nullptr;
     if (nx < 3 || ny < 3 || (long long)nx * (long long)ny > (1LL << 31)) return LBM_ERR_INVALID_ARG;
-    if (model < LBM_BGK || model > LBM_RR || storage < LBM_F64 || storage > LBM_BF16) return LBM_ERR_INVALID_ARG;
+    if (model < LBM_BGK || model > LBM_K_EQ || storage < LBM_F64 || storage > LBM_BF16) return LBM_ERR_INVALID_ARG;
     if (!rates_ok(rates) || !(std::isfinite(rho0) && rho0 > 0.0)) return LBM_ERR_INVALID_ARG;
     if (eq_order < 2 || eq_order > 4) return LBM_ERR_INVALID_ARG;
     if (periodic != 1) return LBM_ERR_UNSUPPORTED;
@@ -1036,7 +1041,7 @@ int lbm_adjoint_run(lbm_ctx* c, long long nsteps, int loss, const double* ux_tar
         return set_err(c, LBM_ERR_UNSUPPORTED, "the adjoint supports FP64/FP32 storage and the extended equilibrium");
     const StepArgs sa = step_args(c);
     lbm::AdjointPlan plan;
-    int rc = lbm::adjoint_plan(c->storage, c->model, c->nx, c->ny, c->pitch, c->plane, sa.w_nu, sa.w3, sa.w4, c->rho0,
+    int rc = lbm::adjoint_plan(c->storage, kernel_model(c->model), cumulant_read(c->model), c->nx, c->ny, c->pitch, c->plane, sa.w_nu, sa.w3, sa.w4, c->rho0,
                                c->urx, c->ury, &plan);
     if (rc) return set_err(c, rc, "no adjoint kernel for this configuration");
     const long long N = nsteps;

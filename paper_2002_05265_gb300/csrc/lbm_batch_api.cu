@@ -230,7 +230,7 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_instance_desc* desc, int 
     for (int k = 0; k < n; ++k) {
         const lbm_instance_desc& d = desc[k];
         if (d.nx < 3 || d.ny < 3 || (long long)d.nx * d.ny > (1LL << 31)) return LBM_ERR_INVALID_ARG;
-        if (d.model < LBM_BGK || d.model > LBM_RR) return LBM_ERR_INVALID_ARG;
+        if (d.model < LBM_BGK || d.model > LBM_K_EQ) return LBM_ERR_INVALID_ARG;
         const lbm_rates& r = d.rates;
         for (double w : {r.omega_nu, r.omega3, r.omega4})
             if (!(std::isfinite(w) && w > 0.0 && w < 2.0)) return LBM_ERR_INVALID_ARG;
@@ -249,8 +249,10 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_instance_desc* desc, int 
         I.a.rho0 = rho0;
         I.a.urx = d.ux_ref;
         I.a.ury = d.uy_ref;
+        // the cumulant readings LBM_K_PRE / LBM_K_EQ: the kernels of LBM_K, other constants
+        I.a.kread = d.model == LBM_K_PRE ? 1 : (d.model == LBM_K_EQ ? 2 : 0);
         lbm::fill_consts(I.a);
-        I.model = d.model;
+        I.model = (d.model == LBM_K_PRE || d.model == LBM_K_EQ) ? LBM_K : d.model;
         I.pad = 0;
         I.ke_ref = d.ke_ref;
         I.ke_factor = d.ke_factor;

@@ -45,8 +45,11 @@ __host__ __device__ inline double shift_of(int i, double rho0, double urx, doubl
 
 // Collision constants, computed once on the host in both precisions (kernels then do no
 // FP64 set-up work, which GB300's narrow FP64 pipe would make costly):
-// [w_nu, w3, w4, rho0, urx, ury, Px0, Px+, Px-, Py0, Py+, Py-, urx^2 + cs^2, ury^2 + cs^2].
-constexpr int kNumConsts = 14;
+// [w_nu, w3, w4, rho0, urx, ury, Px0, Px+, Px-, Py0, Py+, Py-, urx^2 + cs^2, ury^2 + cs^2,
+//  ka, kb, kappa, dkappa/dw_nu] -- ka, kb the cumulant model's coefficients
+// cs^2 (c4 - kappa), c4 - kappa^2 (c4 = 1 - w4; kappa = 1 - w_nu, 1 or 0 for the
+// post-collision, pre-collision or equilibrium rebuild of K~22, field `kread`).
+constexpr int kNumConsts = 18;
 
 struct StepArgs {
     int nx, ny;          // lattice size
@@ -56,16 +59,25 @@ struct StepArgs {
     double w_nu, w3, w4; // relaxation frequencies of orders 2, 3, 4
     double rho0;         // shift reference density
     double urx, ury;     // shift reference velocity
+    int kread;           // cumulant rebuild: 0 post-collision, 1 pre-collision, 2 equilibrium
     double cd[kNumConsts];   // the constants above, FP64 (filled by fill_consts)
     float cf[kNumConsts];    // the same, rounded to FP32
 };
 
+// Second-order central moments of the cumulant model's rebuild of K~22, as a multiple kappa
+// of the non-equilibrium ones n: post-collision (1 - w_nu) n, pre-collision n, equilibrium 0.
+__host__ __device__ inline double cumulant_kappa(int kread, double w_nu) {
+    return kread == 1 ? 1.0 : (kread == 2 ? 0.0 : 1.0 - w_nu);
+}
+
 // Fills the constant tables of a StepArgs from its rates, rho0 and shift velocity.
 __host__ __device__ inline void fill_consts(StepArgs& a) {
+    const double kap = cumulant_kappa(a.kread, a.w_nu), c4 = 1.0 - a.w4;
     const double v[kNumConsts] = {a.w_nu, a.w3, a.w4, a.rho0, a.urx, a.ury,
                                   phi1d(0, a.urx), phi1d(1, a.urx), phi1d(-1, a.urx),
                                   phi1d(0, a.ury), phi1d(1, a.ury), phi1d(-1, a.ury),
-                                  a.urx * a.urx + 1.0 / 3.0, a.ury * a.ury + 1.0 / 3.0};
+                                  a.urx * a.urx + 1.0 / 3.0, a.ury * a.ury + 1.0 / 3.0,
+                                  (c4 - kap) / 3.0, c4 - kap * kap, kap, a.kread == 0 ? -1.0 : 0.0};
     for (int k = 0; k < kNumConsts; ++k) {
         a.cd[k] = v[k];
         a.cf[k] = (float)v[k];
@@ -176,6 +188,7 @@ template <typename T> struct Consts {
     T w, w3, w4, rho0, urx, ury;
     T Px[3], Py[3];      // phi_s(u_ref) for s = 0, +1, -1 (shift factors)
     T Xr, Yr;            // mu_2(u_ref) = u_ref^2 + c_s^2 per axis
+    T ka, kb;            // cumulant coefficients (see kNumConsts)
 };
 template <typename T> __device__ __forceinline__ const T* const_table(const StepArgs& a);
 template <> __device__ __forceinline__ const float* const_table<float>(const StepArgs& a) { return a.cf; }
@@ -189,6 +202,7 @@ __device__ __forceinline__ Consts<T> make_consts(const StepArgs& a) {
     c.Px[0] = t[6]; c.Px[1] = t[7]; c.Px[2] = t[8];
     c.Py[0] = t[9]; c.Py[1] = t[10]; c.Py[2] = t[11];
     c.Xr = t[12]; c.Yr = t[13];
+    c.ka = t[14]; c.kb = t[15];
     return c;
 }
 
@@ -342,14 +356,15 @@ __device__ __forceinline__ void collide(const T (&g)[9], T (&o)[9], const Consts
             D22c += (cs2 * (w - w4)) * (n20 + n02);
         } else if (MODEL != CM) {
             // cumulants: C22 = K22 - (K20 K02 + 2 K11^2)/rho relaxes to 0 and K22* is rebuilt
-            // with the post-collision second-order central moments (written for deviations
-            // from the equilibrium central moments rho c_s^2, 0, rho c_s^4).  With S = n20 + n02,
-            // P = n20 n02 + 2 n11^2 and c = 1 - rate: C22 = k22 - c_s^2 S - P / rho,
-            // K22* = c4 C22 + c_s^2 c2 S + c2^2 P / rho, so
-            // d22 = k22 - K22* = w4 k22 + c_s^2 (c4 - c2) S + (c4 - c2^2) P / rho
-            const T c2 = T(1) - w, c4 = T(1) - w4;
+            // with second-order central moments kappa n (written for deviations from the
+            // equilibrium central moments rho c_s^2, 0, rho c_s^4): kappa = 1 - w for the
+            // post-collision values (the paper's K), 1 or 0 for the pre-collision / equilibrium
+            // readings.  With S = n20 + n02, P = n20 n02 + 2 n11^2 and c4 = 1 - w4:
+            // C22 = k22 - c_s^2 S - P / rho, K22* = c4 C22 + c_s^2 kappa S + kappa^2 P / rho, so
+            // d22 = k22 - K22* = w4 k22 + ka S + kb P / rho with the per-launch constants
+            // ka = c_s^2 (c4 - kappa), kb = c4 - kappa^2
             const T P = n20 * n02 + T(2) * n11 * n11;
-            D22c += (cs2 * (c4 - c2)) * (n20 + n02) + ((c4 - c2 * c2) * P) * irho;
+            D22c += c.ka * (n20 + n02) + (c.kb * irho) * P;
         }
         D22 = D22c;
     }

@@ -83,8 +83,8 @@ struct AdjArgs {
     long long plane;
     double w_nu, w3, w4, rho0;
     double urx, ury;     // storage shift velocity
-    double cd[16];       // collision constants as in StepArgs (fill_consts), FP64 and FP32
-    float cf[16];
+    double cd[18];       // collision constants as in StepArgs (fill_consts), FP64 and FP32
+    float cf[18];
 };
 struct AdjointPlan {
     int storage;            // LBM_F64 or LBM_F32 (lambda kept in the collision precision)
@@ -95,8 +95,8 @@ struct AdjointPlan {
     const void* step_fused; // adjoint step + next segment's forward step in one launch
     int grid_fused, nadj_fused;   // its grid and adjoint blocks (0: not available)
 };
-int adjoint_plan(int storage, int model, int nx, int ny, int pitch, long long plane, double w, double w3, double w4,
-                 double rho0, double urx, double ury, AdjointPlan* p);
+int adjoint_plan(int storage, int model, int kread, int nx, int ny, int pitch, long long plane, double w, double w3,
+                 double w4, double rho0, double urx, double ury, AdjointPlan* p);
 cudaError_t adjoint_launch_fwd(const AdjointPlan& p, const StepArgs& sa, const void* src, void* dst, cudaStream_t s);
 cudaError_t adjoint_launch_step(const AdjointPlan& p, const void* state, const void* lam_in, void* lam_out,
                                 double* rate_part, cudaStream_t s);

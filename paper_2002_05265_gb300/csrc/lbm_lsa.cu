@@ -271,7 +271,7 @@ bool on_device(const void* p) {
 extern "C" int lbm_lsa_growth(int model, lbm_rates rates, int eq_order, const double* flows, int nflows,
                               const double* k, int nk, double* growth, double* eig, double* jac, void* stream) {
     using namespace lbm;
-    if (model < LBM_BGK || model > LBM_RR || !flows || !k || !growth || nflows < 1 || nk < 1 ||
+    if (model < LBM_BGK || model > LBM_K_EQ || !flows || !k || !growth || nflows < 1 || nk < 1 ||
         (long long)nflows * nk > (1LL << 31) || eq_order < 2 || eq_order > 4)
         return LBM_ERR_INVALID_ARG;
     if (eq_order != 4 && model != LBM_BGK) return LBM_ERR_UNSUPPORTED;
@@ -289,6 +289,11 @@ extern "C" int lbm_lsa_growth(int model, lbm_rates rates, int eq_order, const do
     c.rho0 = 1.0;
     c.urx = c.ury = 0.0;
     c.Xr = c.Yr = 1.0 / 3.0;
+    // cumulant readings: LBM_K_PRE / LBM_K_EQ take the K Jacobian with kappa = 1 / 0
+    const int kread = model == LBM_K_PRE ? 1 : (model == LBM_K_EQ ? 2 : 0);
+    c.kap = cumulant_kappa(kread, rates.omega_nu);
+    c.kapw = kread == 0 ? -1.0 : 0.0;
+    if (kread) model = LBM_K;
     double* G = jac;
     int* failed = nullptr;
     cudaError_t e = cudaSuccess;

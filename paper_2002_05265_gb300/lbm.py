@@ -13,7 +13,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
-LBM_BGK, LBM_RM, LBM_HM, LBM_CM, LBM_CHM, LBM_K, LBM_PR, LBM_RR = range(8)
+LBM_BGK, LBM_RM, LBM_HM, LBM_CM, LBM_CHM, LBM_K, LBM_PR, LBM_RR, LBM_K_PRE, LBM_K_EQ = range(10)
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = range(4)
 LBM_PRESET_SRT, LBM_PRESET_REG = 0, 1
 LBM_PATH_AUTO, LBM_PATH_VECTOR, LBM_PATH_BULK = 0, 1, 2
@@ -22,7 +22,7 @@ LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_CUDA, LBM_ERR_BLOWUP, 
     0, -1, -2, -3, -4, -5, -6
 
 MODELS = {"bgk": LBM_BGK, "rm": LBM_RM, "hm": LBM_HM, "cm": LBM_CM, "chm": LBM_CHM, "k": LBM_K,
-          "pr": LBM_PR, "rr": LBM_RR}
+          "pr": LBM_PR, "rr": LBM_RR, "k_pre": LBM_K_PRE, "k_eq": LBM_K_EQ}
 STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
 STORAGE_BYTES = {LBM_F64: 8, LBM_F32: 4, LBM_F16: 2, LBM_BF16: 2}
 

@@ -55,7 +55,7 @@ def test_rates_from_nu(lib):
 
 
 @pytest.mark.parametrize("kw,code", [
-    (dict(nx=2), -1), (dict(ny=1), -1), (dict(model=8), -1), (dict(storage=4), -1),
+    (dict(nx=2), -1), (dict(ny=1), -1), (dict(model=10), -1), (dict(model=-1), -1), (dict(storage=4), -1),
     (dict(rates=(2.0, 1.0, 1.0)), -1), (dict(rates=(1.0, 0.0, 1.0)), -1), (dict(rates=(1.0, 1.0, float("nan"))), -1),
     (dict(eq_order=5), -1), (dict(eq_order=1), -1), (dict(rho0=0.0), -1), (dict(periodic=0), -2),
     (dict(model=4, eq_order=2), -2), (dict(model=1, eq_order=3), -2),

@@ -46,3 +46,17 @@ def test_oracle_row_slabs_reproduce_a_whole_lattice_step():
         whole = olbm.step(f, model, rates)
         slabs = np.concatenate([bench.oracle_slab_step(f, model, rates, y0, 8) for y0 in range(0, 40, 8)], axis=1)
         np.testing.assert_array_equal(slabs, whole)
+
+
+def test_transport_vorticity_is_the_periodic_central_difference():
+    """bench.vorticity (the Sec. 5c vorticity error metric): for u = (-sin(ky y), sin(kx x)) the
+    periodic central differences give exactly omega = sin(kx) cos(kx x) + sin(ky) cos(ky y)
+    (the discrete counterpart of kx cos(kx x) + ky cos(ky y))."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    ny, nx = 48, 64
+    kx, ky = 2 * np.pi * 3 / nx, 2 * np.pi * 2 / ny
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    om = bench.vorticity(-np.sin(ky * y), np.sin(kx * x))
+    np.testing.assert_allclose(om, np.sin(kx) * np.cos(kx * x) + np.sin(ky) * np.cos(ky * y), atol=1e-13)
