@@ -222,7 +222,11 @@ unsigned tile_count(const lbm_ctx* c, int W) {
     return (unsigned)c->ny * (unsigned)((c->nx + W - 1) / W);
 }
 // ring depth of the bulk-copy kernel when the caller chose none
-int default_stages(int) { return 2; }
+// shared-memory stages of the bulk-copy kernel: 4 for the light 16-bit form (one CTA per SM),
+// else 2 (two CTAs per SM)
+int default_stages(int storage, bool light) {
+    return (light && (storage == LBM_F16 || storage == LBM_BF16)) ? 4 : 2;
+}
 
 // true when p is device-accessible memory the kernels may read/write directly
 bool is_device_ptr(const void* p) {
@@ -872,7 +876,7 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
         tile = ctxs[k]->storage == ctxs[0]->storage && ctxs[k]->path != LBM_PATH_VECTOR && row_aligned(ctxs[k]);
     if (tile) {
         const int storage = ctxs[0]->storage;
-        const int stages = ctxs[0]->stages > 0 ? ctxs[0]->stages : default_stages(storage);
+        const int stages = ctxs[0]->stages > 0 ? ctxs[0]->stages : default_stages(storage, light_models(ctxs, n));
         const int W = tile_width(storage);
         unsigned off = 0;
         unsigned units = 0;

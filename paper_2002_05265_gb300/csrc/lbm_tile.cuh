@@ -435,8 +435,20 @@ __device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst,
 // Persistent: CTA b processes tiles b, b + gridDim.x, ...; warp 8 is the producer (one
 // lane issues the copies), warps 0-7 consume.  NS = stages in the ring; FORM = 0 general,
 // 1 the light 16-bit form (BGK, RM, HM, PR only).
+// Resident CTAs per SM the register allocation is sized for: FP64 1; FP32 and the general
+// 16-bit form 2 (96 registers); the light 16-bit form 1 (its packed pass fits in 168
+// registers without spills, and with 4 stages one CTA keeps as many bytes in flight as two
+// did with 2: measured 0.99 of HBM at 16384^2 against 0.97).
+#ifndef LBM_TILE_LIGHT_MINB
+#define LBM_TILE_LIGHT_MINB 1
+#endif
+#ifndef LBM_TILE_GENERAL_MINB
+#define LBM_TILE_GENERAL_MINB 2
+#endif
 template <typename S, bool SHIFT, int NS, int FORM>
-__global__ void __launch_bounds__(kTileThreads, sizeof(S) == 8 ? 1 : 2) tile_step_kernel(const __grid_constant__ TileArgs g) {
+__global__ void __launch_bounds__(kTileThreads,
+                                  sizeof(S) == 8 ? 1 : (FORM == 1 ? LBM_TILE_LIGHT_MINB : LBM_TILE_GENERAL_MINB))
+    tile_step_kernel(const __grid_constant__ TileArgs g) {
     using TS = Tile<S>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * TS::STAGE);
