@@ -192,7 +192,11 @@ const void* pick_tile_kernel(int storage, bool shifted, int stages, bool light) 
         default: return nullptr;
     }
 }
-// the light 16-bit kernel form serves groups whose lattices all run BGK, RM, HM or PR
+#ifndef LBM_LIGHT_MULTI_STEP
+#define LBM_LIGHT_MULTI_STEP 0   // 1: the light form serves multi-step launches too
+#endif
+// the light kernel form (float, half, bfloat16) serves groups whose lattices all run BGK, RM,
+// HM or PR
 bool light_models(lbm_ctx* const* ctxs, int n) {
     for (int k = 0; k < n; ++k) {
         const int m = ctxs[k]->model;
@@ -221,9 +225,9 @@ unsigned tile_count(const lbm_ctx* c, int W) {
     if (R > 1) return (unsigned)((c->ny + R - 1) / R);
     return (unsigned)c->ny * (unsigned)((c->nx + W - 1) / W);
 }
-// ring depth of the bulk-copy kernel when the caller chose none
-// shared-memory stages of the bulk-copy kernel: 4 for the light 16-bit form (one CTA per SM),
-// else 2 (two CTAs per SM)
+// shared-memory stages of the bulk-copy kernel when the caller chose none: 4 for the light
+// 16-bit form (one CTA per SM, half-size stages), else 2 (the light FP32 form: 0.91 of HBM
+// with 4 at 16384^2, 0.98-1.00 with 2)
 int default_stages(int storage, bool light) {
     return (light && (storage == LBM_F16 || storage == LBM_BF16)) ? 4 : 2;
 }
@@ -876,7 +880,6 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
         tile = ctxs[k]->storage == ctxs[0]->storage && ctxs[k]->path != LBM_PATH_VECTOR && row_aligned(ctxs[k]);
     if (tile) {
         const int storage = ctxs[0]->storage;
-        const int stages = ctxs[0]->stages > 0 ? ctxs[0]->stages : default_stages(storage, light_models(ctxs, n));
         const int W = tile_width(storage);
         unsigned off = 0;
         unsigned units = 0;
@@ -904,23 +907,39 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
             tile = false;
         }
         g->ttotal = off;
-        g->tsmem = tile_smem(storage, stages);
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        for (int sh = 0; sh < 2 && tile; ++sh) {
-            const void* k = pick_tile_kernel(storage, sh == 1, stages, light_models(ctxs, n));
-            int per_sm = 0;
-            if (!k || cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, g->tsmem) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, lbm::kTileThreads, g->tsmem) != cudaSuccess ||
-                per_sm < 1) {
-                cudaGetLastError();
-                tile = false;
-                break;
+        // kernels (unshifted, shifted), shared memory and grids of one kernel form; false if
+        // a kernel is missing or cannot be resident
+        auto plan = [&](bool light) {
+            const int stages = ctxs[0]->stages > 0 ? ctxs[0]->stages : default_stages(storage, light);
+            const int smem = tile_smem(storage, stages);
+            const void* kern[2];
+            int grid[2];
+            for (int sh = 0; sh < 2; ++sh) {
+                kern[sh] = pick_tile_kernel(storage, sh == 1, stages, light);
+                int per_sm = 0;
+                if (!kern[sh] || cudaFuncSetAttribute(kern[sh], cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[sh], lbm::kTileThreads, smem) != cudaSuccess ||
+                    per_sm < 1) {
+                    cudaGetLastError();
+                    return false;
+                }
+                grid[sh] = sms * per_sm;   // all resident CTAs (a multi-step launch needs them co-resident)
             }
-            g->tkernel[sh] = k;
-            g->tgrid[sh] = sms * per_sm;   // all resident CTAs (a multi-step launch needs them co-resident)
-        }
+            g->tsmem = smem;
+            for (int sh = 0; sh < 2; ++sh) {
+                g->tkernel[sh] = kern[sh];
+                g->tgrid[sh] = grid[sh];
+            }
+            return true;
+        };
+        // The light form runs one CTA per SM: in a multi-step launch every row-counter wait
+        // would stall its SM, so it serves only groups that the general form's plan steps once
+        // per launch (large lattices).
+        tile = tile && plan(false);
+        if (tile && light_models(ctxs, n) && (LBM_LIGHT_MULTI_STEP || tile_steps_per_launch(g) == 1)) plan(true);
         // the library's choice: a step with fewer tiles than resident CTAs leaves the copy
         // pipeline mostly idle (latency-bound); the register-staged kernels do better there
         bool forced = false;

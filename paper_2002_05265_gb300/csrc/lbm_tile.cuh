@@ -62,9 +62,10 @@ constexpr int kTileThreads = (kTileConsumerWarps + 2) * 32;   // + producer warp
 // Nodes a consumer thread collides per pass (one vector access per population): 16 bytes
 // for FP64 / FP32; for the 16-bit types LBM_TILE_HALF_CV nodes (4: 8-byte accesses, two
 // passes over a tile).
-// 16-bit storage has two forms of the kernel.  The general form (every model) takes the two
-// 4-node passes.  The light form (FORM = 1), used when every lattice of a launch runs BGK, RM,
-// HM or PR, instead takes one pass of 8 nodes per thread with the values kept packed
+// The kernel has two forms.  The general form serves every model.  The light form (FORM = 1)
+// serves one-step launches whose lattices all run BGK, RM, HM or PR and is compiled for one
+// CTA per SM.  In 16-bit storage it also changes the consumer code: instead of the general
+// form's two 4-node passes it takes one pass of 8 nodes per thread with the values kept packed
 // (tile_collide_packed): 16-byte accesses and half the passes, which their short collision
 // affords.  They are separate kernels because the packed path's register pressure makes the
 // compiler spill in the loop every model shares (measured: the central-moment models then lose
@@ -434,11 +435,14 @@ __device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst,
 // ---- the kernel ------------------------------------------------------------------------------
 // Persistent: CTA b processes tiles b, b + gridDim.x, ...; warp 8 is the producer (one
 // lane issues the copies), warps 0-7 consume.  NS = stages in the ring; FORM = 0 general,
-// 1 the light 16-bit form (BGK, RM, HM, PR only).
-// Resident CTAs per SM the register allocation is sized for: FP64 1; FP32 and the general
-// 16-bit form 2 (96 registers); the light 16-bit form 1 (its packed pass fits in 168
-// registers without spills, and with 4 stages one CTA keeps as many bytes in flight as two
-// did with 2: measured 0.99 of HBM at 16384^2 against 0.97).
+// 1 light (BGK, RM, HM, PR only).
+// Resident CTAs per SM the register allocation is sized for: FP64 1; the general FP32 and
+// 16-bit forms 2 (96 registers); the light forms 1 (FP32 110 registers; the packed 16-bit pass
+// 168 registers without spills, with 4 stages one CTA keeping as many bytes in flight as two
+// did with 2).  Measured at 16384^2: FP32 0.98-1.00 of HBM against 0.95-0.96, FP16 0.99-1.02
+// against 0.97.  In a multi-step launch one CTA per SM stalls its SM at every row-counter
+// wait (0.49-0.69 against 0.71-0.97 for groups of eight 1024^2 lattices), hence one-step
+// launches only.
 #ifndef LBM_TILE_LIGHT_MINB
 #define LBM_TILE_LIGHT_MINB 1
 #endif

@@ -108,6 +108,30 @@ def test_bulk_16bit_two_tiles_per_row(L, model, storage):
         assert _l2(bulk, vec) <= bound
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("model", ["bgk", "rm", "hm", "pr"])
+def test_light_form_one_step_launches(L, model, storage):
+    """The light kernel form (lattices of BGK, RM, HM or PR stepped one time step per launch:
+    one CTA per SM, no row-completion counters) on 2072 x 5 (tiles of 1024 / 2048 nodes and a
+    short last one), 200 steps, against the oracle and against the general form's multi-step
+    launches: FP32 within 1e-5 of the oracle's velocity and 1e-6 of the general form's
+    populations; 16-bit within the storage-rounding bound of both."""
+    st = L.STORAGES[storage]
+    fields = flows.vortex(2072, 5, Ma=0.1, radius_frac=0.002, noise=1e-8, seed=24)
+    rates = olbm.rates_from_nu(1e-4, "srt")
+    f0 = olbm.init_equilibrium(*fields)
+    ref = olbm.run(f0, model, rates, 200)
+    light = _run_shaped(L, fields, model, rates, st, 200, 1, L.LBM_ORDER_STEP)
+    general = _run_shaped(L, fields, model, rates, st, 200, 10, L.LBM_ORDER_STEP)
+    if storage == "f32":
+        assert _vel_err(light, ref) <= 1e-5
+        assert float(np.max(np.abs(light - general))) <= 1e-6
+    else:
+        bound = WALK_FACTOR * storage_walk_error(f0, storage, 200)
+        assert _l2(light, ref) <= bound
+        assert _l2(light, general) <= bound
+
+
 def test_bulk_multi_lattice_group(L):
     """Three FP32 lattices of different sizes and models (1 to 3 tiles per row) advanced by
     one bulk-copy launch per step equal the same lattices stepped one by one."""
