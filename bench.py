@@ -89,17 +89,21 @@ def parse():
                    help="time steps per bulk-copy launch (0 = the library's default)")
     p.add_argument("--order", default="auto", choices=["auto", "step", "wave", "block"],
                    help="work order of multi-step bulk-copy launches (auto: wavefront when the state exceeds 64 MB)")
+    p.add_argument("--form", default="auto", choices=["auto", "general", "light", "wide"],
+                   help="kernel form of the bulk-copy kernel (auto: the library's choice)")
     return p.parse_args()
 
 
 PATHS = {"auto": 0, "vector": 1, "bulk": 2}
 ORDERS = {"auto": 0, "step": 1, "wave": 2, "block": 3}
+FORMS = {"auto": 0, "general": 1, "light": 2, "wide": 3}
 
 
 def shape_lattice(lat, args):
     """Kernel family and launch shape of a benchmark lattice from the command line."""
     lat.set_kernel_path(PATHS[args.path], args.stages)
     lat.set_launch_shape(args.launch_steps, ORDERS[args.order])
+    lat.set_tile_form(FORMS[args.form])
 
 
 def dist_setup(args):

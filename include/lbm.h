@@ -230,7 +230,8 @@ int lbm_synchronize(lbm_ctx* ctx);
 
 /* Grid geometry actually used: row pitch in elements (>= nx, multiple of 32), CUDA grid and
  * block sizes of the context's register-staged step kernel (the copy-engine kernel of
- * LBM_PATH_BULK / LBM_PATH_AUTO always runs 320-thread CTAs on every resident slot). */
+ * LBM_PATH_BULK / LBM_PATH_AUTO runs CTAs of 192, 320 or 576 threads, by kernel form, on every
+ * resident slot). */
 int lbm_get_layout(const lbm_ctx* ctx, int* pitch, int* grid, int* block);
 
 /* Kernel family that advances a context (library design choice; the paper has no
@@ -239,8 +240,8 @@ int lbm_get_layout(const lbm_ctx* ctx, int* pitch, int* grid, int* block);
  *                    itself (x-shifted elements by warp shuffles); any nx.
  *   LBM_PATH_BULK    copy-engine staged: cp.async.bulk copies each tile's nine pulled row
  *                    segments into a ring of `stages` (2-4; 0 = default) shared-memory stages
- *                    on mbarriers while eight consumer warps collide earlier tiles; needs
- *                    nx * (bytes per population) to be a multiple of 16.
+ *                    on mbarriers while 4-16 consumer warps (lbm_set_tile_form) collide
+ *                    earlier tiles; needs nx * (bytes per population) to be a multiple of 16.
  *   LBM_PATH_AUTO    BULK where the row length allows it and a time step has at least one
  *                    tile per resident CTA, else VECTOR (the default).
  * Applies to the context's next lbm_step and to groups created afterwards.  Errors:
@@ -253,8 +254,9 @@ int lbm_set_kernel_path(lbm_ctx* ctx, int path, int stages);
  * counterpart; results are identical for every shape).  One launch may advance several time
  * steps: a tile of step s is copied once the rows it pulls from are complete in step s - 1
  * (row-completion counters in device memory, cooperative launch).
- *   steps_per_launch  time steps per launch; 0 = default (16 with the wavefront order; else
- *                     many when a step has fewer than 64 tiles per CTA, 1 otherwise).
+ *   steps_per_launch  time steps per launch; 0 = default (1 in the light and wide forms;
+ *                     in the general form 16 with the wavefront order, else many when a
+ *                     step has fewer than 64 tiles per CTA, 1 otherwise).
  *   order             LBM_ORDER_STEP: every tile of step s before those of step s + 1 (in
  *                     the CTAs' round-robin).  LBM_ORDER_WAVE (lattices of one geometry):
  *                     the steps of a launch interleave, a few rows behind one another, so
@@ -271,6 +273,28 @@ int lbm_set_kernel_path(lbm_ctx* ctx, int path, int stages);
  * unknown order. */
 enum { LBM_ORDER_AUTO = 0, LBM_ORDER_STEP = 1, LBM_ORDER_WAVE = 2, LBM_ORDER_BLOCK = 3 };
 int lbm_set_launch_shape(lbm_ctx* ctx, int steps_per_launch, int order);
+
+/* Kernel form of the copy-engine staged kernel (library design choice; the paper has no
+ * counterpart; results are identical for every form).  The forms differ in consumer warps per
+ * CTA, CTAs per SM and the models compiled in:
+ *   LBM_FORM_GENERAL  every model; 8 consumer warps, 2 CTAs per SM (FP64: 1).  Serves
+ *                     multi-step launches (small lattices), where a CTA that waits on a row
+ *                     counter leaves its SM to the other.
+ *   LBM_FORM_LIGHT    BGK, RM, HM and PR only, FP32 / FP16 / BF16; FP32: 4 consumer warps,
+ *                     2 CTAs per SM; 16-bit: 8 consumer warps, 1 CTA per SM, 8 nodes a thread.
+ *   LBM_FORM_WIDE     every model, FP32 / FP16 / BF16; 16 consumer warps, 1 CTA per SM.
+ *   LBM_FORM_AUTO     the default: the light form when every lattice of the group runs BGK, RM,
+ *                     HM or PR, else the wide form, one time step per launch, where a time step
+ *                     has at least 24 of the form's tiles per resident CTA (or one step per
+ *                     launch is asked for with lbm_set_launch_shape), except that a single
+ *                     lattice the general form would advance in the wavefront order keeps the
+ *                     general form; the general form otherwise (and for FP64).
+ * Applies to the context's next lbm_step and to groups created afterwards (a group takes the
+ * form of its first context when its lattices allow it, else LBM_FORM_AUTO).  Errors:
+ * LBM_ERR_INVALID_ARG for an unknown form; LBM_ERR_UNSUPPORTED for LBM_FORM_LIGHT on another
+ * model or on FP64 storage, or LBM_FORM_WIDE on FP64 storage. */
+enum { LBM_FORM_AUTO = 0, LBM_FORM_GENERAL = 1, LBM_FORM_LIGHT = 2, LBM_FORM_WIDE = 3 };
+int lbm_set_tile_form(lbm_ctx* ctx, int form);
 
 /* Several contexts advanced together, one time step of each in turn (so a set of lattices
  * whose sum exceeds L2 streams from HBM as a single large one would), captured in CUDA

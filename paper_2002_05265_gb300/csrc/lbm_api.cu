@@ -45,6 +45,7 @@ struct lbm_ctx {
     int stages = 0;                    // bulk-copy ring stages, 0 = default
     int launch_steps = 0;              // bulk-copy time steps per launch, 0 = default (lbm_set_launch_shape)
     int launch_order = LBM_ORDER_AUTO; // bulk-copy work order
+    int tile_form = LBM_FORM_AUTO;     // bulk-copy kernel form (lbm_set_tile_form)
     lbm_group* own_group = nullptr;    // used by lbm_step
     unsigned gen = 0;                  // bumped when kernel arguments change (graphs re-record)
     char err[512] = {0};
@@ -57,7 +58,11 @@ struct lbm_group {
     int ggrid[2] = {0, 0};
     std::vector<unsigned> begin;       // padded segment offsets of the contexts
     unsigned padded_total = 0;
-    int tiled = 0;                     // one bulk-copy staged launch per time step
+    int tiled = 0;                     // bulk-copy staged launches
+    int tform = 0;                     // their kernel form: 0 general, 1 light, 2 wide
+    int tone = 0;                      // 1: a form that runs one time step per launch by default
+    int tthreads = 0;                  // CTA size of the form
+    int twidth = 0;                    // nodes per tile of the form
     const void* tkernel[2] = {nullptr, nullptr};   // default shift / reference-velocity shift
     int tgrid[2] = {0, 0};
     int tsmem = 0;                     // dynamic shared memory of the bulk-copy kernel
@@ -183,40 +188,22 @@ const void* pick_group_kernel(int storage, bool shifted) {
 // rows of a whole number of 16-byte chunks: every bulk copy of the tile kernel is aligned
 bool row_aligned(const lbm_ctx* c) { return ((long long)c->nx * lbm::storage_bytes(c->storage)) % 16 == 0; }
 
-const void* pick_tile_kernel(int storage, bool shifted, int stages, bool light) {
+bool pick_tile_kernel(int storage, bool shifted, int stages, int form, lbm::TileKernelInfo* out) {
     switch (storage) {
-        case LBM_F64: return lbm::tile_kernel_f64(shifted, stages, light);
-        case LBM_F32: return lbm::tile_kernel_f32(shifted, stages, light);
-        case LBM_F16: return lbm::tile_kernel_f16(shifted, stages, light);
-        case LBM_BF16: return lbm::tile_kernel_bf16(shifted, stages, light);
-        default: return nullptr;
+        case LBM_F64: return lbm::tile_kernel_f64(shifted, stages, form, out);
+        case LBM_F32: return lbm::tile_kernel_f32(shifted, stages, form, out);
+        case LBM_F16: return lbm::tile_kernel_f16(shifted, stages, form, out);
+        case LBM_BF16: return lbm::tile_kernel_bf16(shifted, stages, form, out);
+        default: return false;
     }
 }
-#ifndef LBM_LIGHT_MULTI_STEP
-#define LBM_LIGHT_MULTI_STEP 0   // 1: the light form serves multi-step launches too
-#endif
 // the light kernel form (float, half, bfloat16) serves groups whose lattices all run BGK, RM,
 // HM or PR
+bool light_model(int m) { return m == LBM_BGK || m == LBM_RM || m == LBM_HM || m == LBM_PR; }
 bool light_models(lbm_ctx* const* ctxs, int n) {
-    for (int k = 0; k < n; ++k) {
-        const int m = ctxs[k]->model;
-        if (m != LBM_BGK && m != LBM_RM && m != LBM_HM && m != LBM_PR) return false;
-    }
+    for (int k = 0; k < n; ++k)
+        if (!light_model(ctxs[k]->model)) return false;
     return true;
-}
-int tile_width(int storage) {
-    switch (storage) {
-        case LBM_F64: return lbm::Tile<double>::W;
-        case LBM_F32: return lbm::Tile<float>::W;
-        default: return lbm::Tile<__half>::W;
-    }
-}
-int tile_smem(int storage, int stages) {
-    switch (storage) {
-        case LBM_F64: return lbm::tile_smem_bytes<double>(stages);
-        case LBM_F32: return lbm::tile_smem_bytes<float>(stages);
-        default: return lbm::tile_smem_bytes<__half>(stages);
-    }
 }
 // rows per row-block tile (>= 2), or 1 for row-segment tiles
 int tile_rows(const lbm_ctx* c, int W) { return 2 * c->nx <= W ? W / c->nx : 1; }
@@ -226,11 +213,19 @@ unsigned tile_count(const lbm_ctx* c, int W) {
     return (unsigned)c->ny * (unsigned)((c->nx + W - 1) / W);
 }
 // shared-memory stages of the bulk-copy kernel when the caller chose none: 4 for the light
-// 16-bit form (one CTA per SM, half-size stages), else 2 (the light FP32 form: 0.91 of HBM
-// with 4 at 16384^2, 0.98-1.00 with 2)
-int default_stages(int storage, bool light) {
-    return (light && (storage == LBM_F16 || storage == LBM_BF16)) ? 4 : 2;
+// 16-bit form (one CTA per SM, half-size stages), else 2 (measured at 16384^2: 3 stages lose
+// 1-2 % in the general and wide forms, and 3 or 4 lose 2-9 % in the light FP32 forms)
+int default_stages(int storage, int form) {
+    return (form == 1 && (storage == LBM_F16 || storage == LBM_BF16)) ? 4 : 2;
 }
+// One-step forms (light, wide): chosen by default when a time step has at least this many
+// tiles per resident CTA; below it the fill and drain of every launch's copy pipeline cost
+// more than the general form's row-counter waits in multi-step launches (measured, FP32
+// groups of 1024^2 lattices: 8 lattices, 27 wide tiles per CTA, 0.97 of the copy bandwidth in
+// the wide form against 0.96 in the general form; 6 lattices, 20 per CTA, 0.95 against 0.96).
+#ifndef LBM_ONE_STEP_TILES_PER_CTA
+#define LBM_ONE_STEP_TILES_PER_CTA 24
+#endif
 
 // true when p is device-accessible memory the kernels may read/write directly
 bool is_device_ptr(const void* p) {
@@ -314,7 +309,7 @@ cudaError_t launch_tile(lbm_group* g, const void* const* buf0, void* const* buf1
     ta.nsteps = nsteps;
     ta.flag = g->ctx[0]->status + 1;   // second int of the first context's status word
     ta.cnt = g->cnt;
-    const int W = tile_width(g->ctx[0]->storage);
+    const int W = g->twidth;
     for (size_t k = 0; k < g->ctx.size(); ++k) {
         lbm_ctx* c = g->ctx[k];
         lbm::TileEntry& e = ta.e[k];
@@ -369,7 +364,7 @@ cudaError_t launch_tile(lbm_group* g, const void* const* buf0, void* const* buf1
     if (ta.wave == 1 && grid > 1 && (grid % 2) == 0) grid -= 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(lbm::kTileThreads);
+    cfg.blockDim = dim3(g->tthreads);
     cfg.dynamicSmemBytes = (size_t)g->tsmem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -427,12 +422,15 @@ int group_step_once(lbm_group* g, cudaStream_t s) {
 
 // Steps per launch of a tiled group: a launch whose step has few tiles per CTA loses a
 // noticeable share of its time to ramping up and draining the copy pipeline, so such groups
-// run many steps per launch (with the row-completion counters); large lattices run one step
-// per launch, where the counters' fences would only add latency to the copy pipeline.
+// run many steps per launch in the general form (with the row-completion counters); the
+// one-step forms (light, wide) and large lattices run one step per launch, where the
+// counters' fences would only add latency to the copy pipeline.
 int tile_steps_per_launch(const lbm_group* g) {
     int per;
     if (g->ctx[0]->launch_steps > 0) {
         per = g->ctx[0]->launch_steps;
+    } else if (g->tone) {
+        per = 1;
     } else if (use_wave(g)) {
         per = 16;   // wavefront: the intermediate states stay in the L2
     } else {
@@ -858,6 +856,22 @@ int lbm_set_launch_shape(lbm_ctx* c, int steps_per_launch, int order) {
     return LBM_OK;
 }
 
+int lbm_set_tile_form(lbm_ctx* c, int form) {
+    if (!c) return LBM_ERR_INVALID_ARG;
+    if (form < LBM_FORM_AUTO || form > LBM_FORM_WIDE) return set_err(c, LBM_ERR_INVALID_ARG, "unknown kernel form");
+    if (form == LBM_FORM_LIGHT && (c->storage == LBM_F64 || !light_model(c->model)))
+        return set_err(c, LBM_ERR_UNSUPPORTED, "the light form serves BGK, RM, HM and PR in FP32 / 16-bit storage");
+    if (form == LBM_FORM_WIDE && c->storage == LBM_F64)
+        return set_err(c, LBM_ERR_UNSUPPORTED, "FP64 storage has the general form only");
+    c->tile_form = form;
+    if (c->own_group) {   // rebuilt at the next lbm_step
+        lbm_group_destroy(c->own_group);
+        c->own_group = nullptr;
+    }
+    c->gen += 1;
+    return LBM_OK;
+}
+
 int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_steps) {
     if (!out || !ctxs || n < 1 || graph_steps < 0 || (graph_steps % 2) != 0) return LBM_ERR_INVALID_ARG;
     *out = nullptr;
@@ -880,77 +894,104 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
         tile = ctxs[k]->storage == ctxs[0]->storage && ctxs[k]->path != LBM_PATH_VECTOR && row_aligned(ctxs[k]);
     if (tile) {
         const int storage = ctxs[0]->storage;
-        const int W = tile_width(storage);
-        unsigned off = 0;
-        unsigned units = 0;
-        g->same_geometry = 1;
-        for (int k = 0; k < n; ++k) {
-            g->tbegin.push_back(off);
-            off += tile_count(ctxs[k], W);
-            g->cbase.push_back(units);
-            const int R = tile_rows(ctxs[k], W);
-            const int U = R > 1 ? (ctxs[k]->ny + R - 1) / R : ctxs[k]->ny;
-            const int ntx = R > 1 ? 1 : (ctxs[k]->nx + W - 1) / W;
-            units += (unsigned)U;
-            if (k == 0) {
-                g->wU = U;
-                g->wntx = ntx;
-            } else if (U != g->wU || ntx != g->wntx || R != tile_rows(ctxs[0], W)) {
-                g->same_geometry = 0;
-            }
-            g->state_bytes += 2LL * 9 * ctxs[k]->plane * lbm::storage_bytes(storage);
-        }
-        g->cunits = units;
-        if (cudaMalloc(&g->cnt, sizeof(unsigned) * units) != cudaSuccess) {
-            cudaGetLastError();
-            g->cnt = nullptr;
-            tile = false;
-        }
-        g->ttotal = off;
+        for (int k = 0; k < n; ++k) g->state_bytes += 2LL * 9 * ctxs[k]->plane * lbm::storage_bytes(storage);
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        // kernels (unshifted, shifted), shared memory and grids of one kernel form; false if
-        // a kernel is missing or cannot be resident
-        auto plan = [&](bool light) {
-            const int stages = ctxs[0]->stages > 0 ? ctxs[0]->stages : default_stages(storage, light);
-            const int smem = tile_smem(storage, stages);
-            const void* kern[2];
+        // kernels (unshifted, shifted), shared memory, grids and tile geometry of one kernel
+        // form; false if a kernel is missing or cannot be resident
+        auto plan = [&](int form) {
+            const int stages = ctxs[0]->stages > 0 ? ctxs[0]->stages : default_stages(storage, form);
+            lbm::TileKernelInfo info[2];
             int grid[2];
             for (int sh = 0; sh < 2; ++sh) {
-                kern[sh] = pick_tile_kernel(storage, sh == 1, stages, light);
                 int per_sm = 0;
-                if (!kern[sh] || cudaFuncSetAttribute(kern[sh], cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[sh], lbm::kTileThreads, smem) != cudaSuccess ||
+                if (!pick_tile_kernel(storage, sh == 1, stages, form, &info[sh]) ||
+                    cudaFuncSetAttribute(info[sh].kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, info[sh].smem) != cudaSuccess ||
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, info[sh].kernel, info[sh].threads, info[sh].smem) != cudaSuccess ||
                     per_sm < 1) {
                     cudaGetLastError();
                     return false;
                 }
                 grid[sh] = sms * per_sm;   // all resident CTAs (a multi-step launch needs them co-resident)
             }
-            g->tsmem = smem;
+            g->tform = form;
+            g->tthreads = info[0].threads;
+            g->twidth = info[0].width;
+            g->tsmem = info[0].smem;
             for (int sh = 0; sh < 2; ++sh) {
-                g->tkernel[sh] = kern[sh];
+                g->tkernel[sh] = info[sh].kernel;
                 g->tgrid[sh] = grid[sh];
             }
+            // tiles (rows or row blocks of the form's width) and completion counters per lattice
+            const int W = g->twidth;
+            unsigned off = 0, units = 0;
+            g->tbegin.clear();
+            g->cbase.clear();
+            g->same_geometry = 1;
+            for (int k = 0; k < n; ++k) {
+                g->tbegin.push_back(off);
+                off += tile_count(ctxs[k], W);
+                g->cbase.push_back(units);
+                const int R = tile_rows(ctxs[k], W);
+                const int U = R > 1 ? (ctxs[k]->ny + R - 1) / R : ctxs[k]->ny;
+                const int ntx = R > 1 ? 1 : (ctxs[k]->nx + W - 1) / W;
+                units += (unsigned)U;
+                if (k == 0) {
+                    g->wU = U;
+                    g->wntx = ntx;
+                } else if (U != g->wU || ntx != g->wntx || R != tile_rows(ctxs[0], W)) {
+                    g->same_geometry = 0;
+                }
+            }
+            g->ttotal = off;
+            g->cunits = units;
             return true;
         };
-        // The light form runs one CTA per SM: in a multi-step launch every row-counter wait
-        // would stall its SM, so it serves only groups that the general form's plan steps once
-        // per launch (large lattices).
-        tile = tile && plan(false);
-        if (tile && light_models(ctxs, n) && (LBM_LIGHT_MULTI_STEP || tile_steps_per_launch(g) == 1)) plan(true);
+        // The form (the first context's choice, lbm_set_tile_form, where the group's lattices
+        // allow it).  By default the one-step form of the group's models (light for BGK, RM, HM,
+        // PR, else wide) when one step per launch is asked for, or when a step has at least
+        // LBM_ONE_STEP_TILES_PER_CTA of that form's tiles per resident CTA and no multi-step
+        // work order is asked for -- except that the wide form leaves a single lattice to the
+        // general form's wavefront launches where those apply (measured, FP32: 4096^2 0.96 of
+        // the copy bandwidth in the wavefront against 0.91 in the wide form; 8192^2 wide 0.96
+        // against 0.94 for the general form's one-step launches); otherwise the general form.
+        const bool light = storage != LBM_F64 && light_models(ctxs, n);
+        const int one_form = storage == LBM_F64 ? -1 : (light ? 1 : 2);
+        const lbm_ctx* c0 = ctxs[0];
+        int form = -1;
+        if (c0->tile_form == LBM_FORM_GENERAL || storage == LBM_F64) {
+            form = 0;
+        } else if (c0->tile_form == LBM_FORM_LIGHT && light) {
+            form = 1;
+        } else if (c0->tile_form == LBM_FORM_WIDE) {
+            form = 2;
+        } else if (c0->launch_steps <= 1 && c0->launch_order != LBM_ORDER_WAVE && c0->launch_order != LBM_ORDER_BLOCK) {
+            const bool general_wave = c0->launch_steps == 0 && plan(0) && use_wave(g);
+            if ((one_form == 1 || !general_wave) && plan(one_form)) {
+                const int grid = std::max(g->tgrid[0], g->tgrid[1]);
+                if (c0->launch_steps == 1 || g->ttotal >= (unsigned)LBM_ONE_STEP_TILES_PER_CTA * (unsigned)grid)
+                    form = one_form;
+            }
+        }
+        if (form < 0) form = 0;
+        tile = plan(form);
+        g->tone = tile && form != 0 ? 1 : 0;
         // the library's choice: a step with fewer tiles than resident CTAs leaves the copy
         // pipeline mostly idle (latency-bound); the register-staged kernels do better there
         bool forced = false;
         for (int k = 0; k < n; ++k) forced = forced || ctxs[k]->path == LBM_PATH_BULK;
-        if (tile && !forced && off < (unsigned)std::max(g->tgrid[0], g->tgrid[1])) tile = false;
+        if (tile && !forced && g->ttotal < (unsigned)std::max(g->tgrid[0], g->tgrid[1])) tile = false;
+        if (tile && cudaMalloc(&g->cnt, sizeof(unsigned) * g->cunits) != cudaSuccess) {
+            cudaGetLastError();
+            g->cnt = nullptr;
+            tile = false;
+        }
         if (!tile) {
             g->tbegin.clear();
             g->cbase.clear();
             g->ttotal = 0;
-            if (g->cnt) cudaFree(g->cnt);
-            g->cnt = nullptr;
+            g->tone = 0;
         }
         g->tiled = tile ? 1 : 0;
     }

@@ -20,13 +20,19 @@ const void* group_kernel_f16(bool shifted);
 const void* group_kernel_bf16(bool shifted);
 
 // Bulk-copy staged step kernel (tile_step_kernel<S, shifted, stages, form>, one TileArgs
-// parameter, kTileThreads threads, tile_smem_bytes dynamic shared memory) per storage; stages
-// 2-4; `light` selects the 16-bit form for launches whose lattices all run BGK, RM, HM or PR
-// (ignored for FP64 / FP32).
-const void* tile_kernel_f64(bool shifted, int stages, bool light);
-const void* tile_kernel_f32(bool shifted, int stages, bool light);
-const void* tile_kernel_f16(bool shifted, int stages, bool light);
-const void* tile_kernel_bf16(bool shifted, int stages, bool light);
+// parameter) per storage; stages 2-4; form 0 general (every model, several CTAs per SM),
+// 1 light (lattices that all run BGK, RM, HM or PR; one-step launches), 2 wide (every model,
+// one CTA per SM; one-step launches).  FP64 has form 0 only.  False if not instantiated.
+struct TileKernelInfo {
+    const void* kernel;
+    int threads;   // CTA size
+    int width;     // nodes per tile (W)
+    int smem;      // dynamic shared memory bytes
+};
+bool tile_kernel_f64(bool shifted, int stages, int form, TileKernelInfo* out);
+bool tile_kernel_f32(bool shifted, int stages, int form, TileKernelInfo* out);
+bool tile_kernel_f16(bool shifted, int stages, int form, TileKernelInfo* out);
+bool tile_kernel_bf16(bool shifted, int stages, int form, TileKernelInfo* out);
 
 // Batched persistent sweep kernel for (vector width, CTA size); nullptr if not instantiated.
 const void* batch_kernel_f64(int vec, int block);

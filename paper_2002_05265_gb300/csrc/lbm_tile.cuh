@@ -1,9 +1,10 @@
 // Bulk-copy staged step kernel: the copy engine (cp.async.bulk, completing on mbarriers)
 // streams the nine pulled row segments of each tile into a ring of shared-memory stages
-// while eight consumer warps collide the previous tiles from shared memory and store their
-// results straight to HBM.  Loads stay in flight independently of the collision arithmetic,
-// which the register-staged kernels of lbm_device.cuh cannot do once the per-node
-// arithmetic is long (16-bit storage, central-moment models).
+// while the consumer warps (4, 8 or 16 per CTA, by kernel form) collide the previous tiles
+// from shared memory and store their results straight to HBM.  Loads stay in flight
+// independently of the collision arithmetic, which the register-staged kernels of
+// lbm_device.cuh cannot do once the per-node arithmetic is long (16-bit storage,
+// central-moment models).
 //
 // Two tile shapes, chosen per lattice:
 //  * segment tiles (nx > W/2): one row segment of up to W consecutive nodes (the last
@@ -24,7 +25,7 @@
 // copied only when the rows it pulls from (its own and the neighbouring rows or row blocks)
 // are complete in step s - 1.  A signal warp (one lane) follows the consumers: each consumer
 // warp, after its stores, adds one to its stage's completion count in shared memory (release
-// at CTA scope); when the count shows all eight warps done with a tile, the signal lane
+// at CTA scope); when the count shows all consumer warps done with a tile, the signal lane
 // issues a GPU-scope fence (cumulative over those stores) and adds one to the tile's per-row
 // (per row-block) counter in global memory.  It runs beside the copy pipeline, never gating
 // it: the producer reuses a stage as soon as the consumers release it (mbarrier `empty`),
@@ -56,27 +57,42 @@
 
 namespace lbm {
 
-constexpr int kTileConsumerWarps = 8;
-constexpr int kTileThreads = (kTileConsumerWarps + 2) * 32;   // + producer warp + signal warp
-
+// Kernel forms.  Every form runs the same pipeline (one producer warp, CW consumer warps, one
+// signal warp per CTA); they differ in the consumer warps per CTA, the resident CTAs per SM the
+// registers are sized for, and the models compiled in:
+//  * FORM 0, general: every model, 8 consumer warps, 2 CTAs per SM (FP64: 1).  Serves
+//    multi-step launches (groups of small lattices, the adjoint's recomputation), where the
+//    row-counter waits want several CTAs per SM.
+//  * FORM 1, light: one-step launches whose lattices all run BGK, RM, HM or PR.  FP32: 4
+//    consumer warps and 2 CTAs per SM with 115 registers (tiles of 512 nodes; measured 1.02 of
+//    the copy bandwidth at 16384^2 and 1.01 at 4096^2, against 0.98-0.99 for 8 warps at 1 CTA
+//    per SM, 0.94 for 4 warps at 3 CTAs per SM with 96 registers, 0.95 for the general form).
+//    16-bit: 8 consumer warps at 1 CTA per SM and one pass of 8 nodes per thread with the values
+//    kept packed (tile_collide_packed): 16-byte accesses and half the passes, which their short
+//    collision affords.  It is a separate kernel because the packed path's register pressure
+//    makes the compiler spill in the loop every model shares (measured: the central-moment
+//    models then lose 2-4 %, and with 8 nodes at once themselves 3-6 %).
+//  * FORM 2, wide: every model, 16 consumer warps at 1 CTA per SM (tiles of 8 KB a plane).
+//    Serves one-step launches of the other groups: at 16384^2 the central-moment models run at
+//    0.98-0.99 (FP32) and 0.99-1.02 (16-bit) of the copy bandwidth, against 0.95-0.96 and
+//    0.96-0.99 in the general form; the benchmark's eight 1024^2 lattices one step per launch
+//    at 0.97, against 0.95 in the general form's 100-step launches.  In multi-step launches the
+//    single CTA stalls its SM at every row-counter wait (0.83), so those keep the general form.
 // Nodes a consumer thread collides per pass (one vector access per population): 16 bytes
 // for FP64 / FP32; for the 16-bit types LBM_TILE_HALF_CV nodes (4: 8-byte accesses, two
 // passes over a tile).
-// The kernel has two forms.  The general form serves every model.  The light form (FORM = 1)
-// serves one-step launches whose lattices all run BGK, RM, HM or PR and is compiled for one
-// CTA per SM.  In 16-bit storage it also changes the consumer code: instead of the general
-// form's two 4-node passes it takes one pass of 8 nodes per thread with the values kept packed
-// (tile_collide_packed): 16-byte accesses and half the passes, which their short collision
-// affords.  They are separate kernels because the packed path's register pressure makes the
-// compiler spill in the loop every model shares (measured: the central-moment models then lose
-// 2-4 %, and with 8 nodes at once themselves 3-6 %).
 #ifndef LBM_TILE_HALF_CV
 #define LBM_TILE_HALF_CV 4
 #endif
-template <typename S> struct Tile {
+template <typename S, int FORM> struct TileForm {
+    static constexpr int CW = FORM == 2 ? 16 : ((FORM == 1 && sizeof(S) == 4) ? 4 : 8);   // consumer warps
+    static constexpr int MINB = sizeof(S) == 8 ? 1 : (FORM == 0 ? 2 : ((FORM == 1 && sizeof(S) == 4) ? 2 : 1));
+    static constexpr int THREADS = (CW + 2) * 32;   // + producer warp + signal warp
+};
+template <typename S, int CW> struct Tile {
     static constexpr int VEC = (sizeof(S) == 2) ? LBM_TILE_HALF_CV : 16 / (int)sizeof(S);
-    static constexpr int W = kTileConsumerWarps * 32 * 16 / (int)sizeof(S);   // nodes per tile (4 KB a plane)
-    static constexpr int PASSES = W / (kTileConsumerWarps * 32 * VEC);         // consumer passes per tile
+    static constexpr int W = CW * 32 * 16 / (int)sizeof(S);   // nodes per tile (CW / 2 KB a plane)
+    static constexpr int PASSES = W / (CW * 32 * VEC);         // consumer passes per tile
     static constexpr int H = 16 / (int)sizeof(S);              // elements of one halo chunk
     static constexpr int PLANE = (W + 2 * H) * (int)sizeof(S); // bytes of one population slot
     static constexpr int STAGE = 9 * PLANE;                    // bytes of one stage
@@ -205,7 +221,7 @@ struct TilePos {
     int rows;   // rows in the tile (1 for segment tiles)
     int unit;   // completion counter of the tile within its lattice: row, or row block
 };
-template <typename S>
+template <int W>   // W: nodes per tile of the kernel form
 __device__ __forceinline__ TilePos tile_pos(const TileArgs& g, unsigned t) {
     TilePos q;
     int e = 0;
@@ -215,8 +231,8 @@ __device__ __forceinline__ TilePos tile_pos(const TileArgs& g, unsigned t) {
     q.e = e;
     if (E.ntx > 0) {
         q.y = (int)(lt / (unsigned)E.ntx);
-        q.x0 = (int)(lt - (unsigned)q.y * (unsigned)E.ntx) * Tile<S>::W;
-        q.w = min(Tile<S>::W, E.a.nx - q.x0);
+        q.x0 = (int)(lt - (unsigned)q.y * (unsigned)E.ntx) * W;
+        q.w = min(W, E.a.nx - q.x0);
         q.rows = 1;
         q.unit = q.y;
     } else {
@@ -260,11 +276,11 @@ __device__ __forceinline__ unsigned item_count(const TileArgs& g) {
 }
 
 // ---- consumer: collide VEC nodes of a staged tile --------------------------------------------
-template <int MODEL, int EQ, typename S, bool SHIFT>
+template <int MODEL, int EQ, typename S, bool SHIFT, int CW>
 __device__ __forceinline__ void tile_collide(const unsigned char* stage, S* dstbuf, const TileEntry& E, const TilePos& q,
                                              int p) {
     using T = typename Conv<S>::T;
-    constexpr int VEC = Tile<S>::VEC;
+    constexpr int VEC = Tile<S, CW>::VEC;
     const Consts<T> c = make_consts<T>(E.a);
     // slot indices of the elements one node left of p and one node right of p + VEC - 1:
     // the halo chunks for segment tiles, the other end of the same row for row-block tiles
@@ -278,7 +294,7 @@ __device__ __forceinline__ void tile_collide(const unsigned char* stage, S* dstb
     T f[9][VEC];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const S* b = reinterpret_cast<const S*>(stage + i * Tile<S>::PLANE + 16);
+        const S* b = reinterpret_cast<const S*>(stage + i * Tile<S, CW>::PLANE + 16);
         T v[VEC];
         vload<S, VEC>(b + p, v);
         if (ex_of(i) == 0) {
@@ -334,7 +350,7 @@ template <> struct Half16<__nv_bfloat16> {
     __device__ static __forceinline__ float one(__nv_bfloat16 s) { return __bfloat162float(s); }
 };
 
-template <int MODEL, int EQ, typename S, bool SHIFT>
+template <int MODEL, int EQ, typename S, bool SHIFT, int CW>
 __device__ __forceinline__ void tile_collide_packed(const unsigned char* stage, S* dstbuf, const TileEntry& E,
                                                     const TilePos& q, int p) {
     constexpr int VEC = 8;
@@ -350,7 +366,7 @@ __device__ __forceinline__ void tile_collide_packed(const unsigned char* stage, 
     float edge[9];   // the element one node left (xi_x = +1) or right (xi_x = -1) of the 8
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const S* b = reinterpret_cast<const S*>(stage + i * Tile<S>::PLANE + 16);
+        const S* b = reinterpret_cast<const S*>(stage + i * Tile<S, CW>::PLANE + 16);
         const uint4 v = *reinterpret_cast<const uint4*>(b + p);
         in[i][0] = v.x; in[i][1] = v.y; in[i][2] = v.z; in[i][3] = v.w;
         edge[i] = ex_of(i) == 1 ? Half16<S>::one(b[li]) : (ex_of(i) == -1 ? Half16<S>::one(b[ri]) : 0.0f);
@@ -381,79 +397,72 @@ __device__ __forceinline__ void tile_collide_packed(const unsigned char* stage, 
 }
 
 // Collides every node of a staged tile that this consumer thread owns.
-template <int MODEL, int EQ, typename S, bool SHIFT, bool PACKED>
+template <int MODEL, int EQ, typename S, bool SHIFT, bool PACKED, int CW>
 __device__ __forceinline__ void tile_collide_all(const unsigned char* stage, S* dst, const TileEntry& E,
                                                  const TilePos& q) {
-    using TS = Tile<S>;
+    using TS = Tile<S, CW>;
     if constexpr (PACKED && sizeof(S) == 2) {
+        static_assert(TS::W == CW * 32 * 8, "one packed pass of 8 nodes per consumer thread covers the tile");
         const int p = (int)threadIdx.x * 8;
-        if (p < q.w * q.rows) tile_collide_packed<MODEL, EQ, S, SHIFT>(stage, dst, E, q, p);
+        if (p < q.w * q.rows) tile_collide_packed<MODEL, EQ, S, SHIFT, CW>(stage, dst, E, q, p);
     } else {
         // the passes are not unrolled: unrolled, the consumers' code of one model outgrows the
         // instruction cache (ncu, 16-bit K at 8192^2: 2.6x the fetch stalls of CHM, 0.926 of
         // HBM; rolled: the stalls of CHM, 0.956)
 #pragma unroll 1
         for (int pass = 0; pass < TS::PASSES; ++pass) {
-            const int p = (pass * kTileConsumerWarps * 32 + (int)threadIdx.x) * TS::VEC;
-            if (p < q.w * q.rows) tile_collide<MODEL, EQ, S, SHIFT>(stage, dst, E, q, p);
+            const int p = (pass * CW * 32 + (int)threadIdx.x) * TS::VEC;
+            if (p < q.w * q.rows) tile_collide<MODEL, EQ, S, SHIFT, CW>(stage, dst, E, q, p);
         }
     }
 }
 
 template <typename S, bool SHIFT, int FORM>
 __device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst, const TileEntry& E, const TilePos& q) {
+    constexpr int CW = TileForm<S, FORM>::CW;
     if constexpr (FORM == 1) {
         // light form: only the models it is launched for
         switch (E.model) {
             case BGK:
-                if (E.eq_order == 2) tile_collide_all<BGK, 2, S, SHIFT, true>(stage, dst, E, q);
-                else if (E.eq_order == 3) tile_collide_all<BGK, 3, S, SHIFT, true>(stage, dst, E, q);
-                else tile_collide_all<BGK, 4, S, SHIFT, true>(stage, dst, E, q);
+                if (E.eq_order == 2) tile_collide_all<BGK, 2, S, SHIFT, true, CW>(stage, dst, E, q);
+                else if (E.eq_order == 3) tile_collide_all<BGK, 3, S, SHIFT, true, CW>(stage, dst, E, q);
+                else tile_collide_all<BGK, 4, S, SHIFT, true, CW>(stage, dst, E, q);
                 break;
-            case RM: tile_collide_all<RM, 4, S, SHIFT, true>(stage, dst, E, q); break;
-            case HM: tile_collide_all<HM, 4, S, SHIFT, true>(stage, dst, E, q); break;
-            default: tile_collide_all<PR, 4, S, SHIFT, true>(stage, dst, E, q); break;
+            case RM: tile_collide_all<RM, 4, S, SHIFT, true, CW>(stage, dst, E, q); break;
+            case HM: tile_collide_all<HM, 4, S, SHIFT, true, CW>(stage, dst, E, q); break;
+            default: tile_collide_all<PR, 4, S, SHIFT, true, CW>(stage, dst, E, q); break;
         }
         return;
     }
     switch (E.model) {
         case BGK:
-            if (E.eq_order == 2) tile_collide_all<BGK, 2, S, SHIFT, false>(stage, dst, E, q);
-            else if (E.eq_order == 3) tile_collide_all<BGK, 3, S, SHIFT, false>(stage, dst, E, q);
-            else tile_collide_all<BGK, 4, S, SHIFT, false>(stage, dst, E, q);
+            if (E.eq_order == 2) tile_collide_all<BGK, 2, S, SHIFT, false, CW>(stage, dst, E, q);
+            else if (E.eq_order == 3) tile_collide_all<BGK, 3, S, SHIFT, false, CW>(stage, dst, E, q);
+            else tile_collide_all<BGK, 4, S, SHIFT, false, CW>(stage, dst, E, q);
             break;
-        case RM: tile_collide_all<RM, 4, S, SHIFT, false>(stage, dst, E, q); break;
-        case HM: tile_collide_all<HM, 4, S, SHIFT, false>(stage, dst, E, q); break;
-        case CM: tile_collide_all<CM, 4, S, SHIFT, false>(stage, dst, E, q); break;
-        case CHM: tile_collide_all<CHM, 4, S, SHIFT, false>(stage, dst, E, q); break;
-        case CUM: tile_collide_all<CUM, 4, S, SHIFT, false>(stage, dst, E, q); break;
-        case PR: tile_collide_all<PR, 4, S, SHIFT, false>(stage, dst, E, q); break;
-        default: tile_collide_all<RR, 4, S, SHIFT, false>(stage, dst, E, q); break;
+        case RM: tile_collide_all<RM, 4, S, SHIFT, false, CW>(stage, dst, E, q); break;
+        case HM: tile_collide_all<HM, 4, S, SHIFT, false, CW>(stage, dst, E, q); break;
+        case CM: tile_collide_all<CM, 4, S, SHIFT, false, CW>(stage, dst, E, q); break;
+        case CHM: tile_collide_all<CHM, 4, S, SHIFT, false, CW>(stage, dst, E, q); break;
+        case CUM: tile_collide_all<CUM, 4, S, SHIFT, false, CW>(stage, dst, E, q); break;
+        case PR: tile_collide_all<PR, 4, S, SHIFT, false, CW>(stage, dst, E, q); break;
+        default: tile_collide_all<RR, 4, S, SHIFT, false, CW>(stage, dst, E, q); break;
     }
 }
 
 // ---- the kernel ------------------------------------------------------------------------------
-// Persistent: CTA b processes tiles b, b + gridDim.x, ...; warp 8 is the producer (one
-// lane issues the copies), warps 0-7 consume.  NS = stages in the ring; FORM = 0 general,
-// 1 light (BGK, RM, HM, PR only).
-// Resident CTAs per SM the register allocation is sized for: FP64 1; the general FP32 and
-// 16-bit forms 2 (96 registers); the light forms 1 (FP32 110 registers; the packed 16-bit pass
-// 168 registers without spills, with 4 stages one CTA keeping as many bytes in flight as two
-// did with 2).  Measured at 16384^2: FP32 0.98-1.00 of HBM against 0.95-0.96, FP16 0.99-1.02
-// against 0.97.  In a multi-step launch one CTA per SM stalls its SM at every row-counter
-// wait (0.49-0.69 against 0.71-0.97 for groups of eight 1024^2 lattices), hence one-step
-// launches only.
-#ifndef LBM_TILE_LIGHT_MINB
-#define LBM_TILE_LIGHT_MINB 1
-#endif
-#ifndef LBM_TILE_GENERAL_MINB
-#define LBM_TILE_GENERAL_MINB 2
-#endif
+// Persistent: CTA b processes tiles b, b + gridDim.x, ...; warps 0 .. CW - 1 consume, warp CW
+// is the producer (one lane issues the copies), warp CW + 1 the signal warp.  NS = stages in
+// the ring; FORM as in TileForm.  Registers (no spills): general FP32 / 16-bit 96, wide 96,
+// light FP32 115, light 16-bit 168 (the packed pass; with 4 stages one CTA keeps as many bytes
+// in flight as two did with 2).  In a multi-step launch one CTA per SM stalls its SM at every
+// row-counter wait (0.49-0.83 against 0.71-0.97 for groups of eight 1024^2 lattices), hence
+// the single-CTA forms serve one-step launches.
 template <typename S, bool SHIFT, int NS, int FORM>
-__global__ void __launch_bounds__(kTileThreads,
-                                  sizeof(S) == 8 ? 1 : (FORM == 1 ? LBM_TILE_LIGHT_MINB : LBM_TILE_GENERAL_MINB))
+__global__ void __launch_bounds__(TileForm<S, FORM>::THREADS, TileForm<S, FORM>::MINB)
     tile_step_kernel(const __grid_constant__ TileArgs g) {
-    using TS = Tile<S>;
+    constexpr int CW = TileForm<S, FORM>::CW;
+    using TS = Tile<S, CW>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * TS::STAGE);
     uint64_t* empty = full + NS;
@@ -462,7 +471,7 @@ __global__ void __launch_bounds__(kTileThreads,
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_addr(&full[s]), 1);
-            mbar_init(smem_addr(&empty[s]), kTileConsumerWarps);
+            mbar_init(smem_addr(&empty[s]), CW);
             done[s] = 0u;
         }
         mbar_init_fence();
@@ -471,7 +480,7 @@ __global__ void __launch_bounds__(kTileThreads,
     // CTA b takes work items b, b + gridDim.x, ... (all three roles in the same order)
     const unsigned items = item_count(g);
 
-    if (warp == kTileConsumerWarps + 1) {
+    if (warp == CW + 1) {
         if (lane != 0 || g.nsteps == 1) return;   // a single-step launch has no dependencies
         // ---------------- signal ----------------
         int k = 0;
@@ -480,7 +489,7 @@ __global__ void __launch_bounds__(kTileThreads,
             unsigned t;
             if (!item_at(g, i, step, t)) continue;
             const int st = k % NS;
-            const unsigned need = (unsigned)kTileConsumerWarps * (unsigned)(k / NS + 1);
+            const unsigned need = (unsigned)CW * (unsigned)(k / NS + 1);
             // all consumer warps done with this tile (monotone count: lagging is harmless)
             bool ok = smem_ld_acquire(&done[st]) >= need;
             if (!ok) {
@@ -496,7 +505,7 @@ __global__ void __launch_bounds__(kTileThreads,
                 return;
             }
             if (step + 1 < g.nsteps) {
-                const TilePos q = tile_pos<S>(g, t);
+                const TilePos q = tile_pos<TS::W>(g, t);
                 fence_acq_rel_gpu();   // the consumers' stores, ordered before by the count
                 red_add_relaxed(g.cnt + g.e[q.e].cbase + q.unit, 1u);
             }
@@ -505,7 +514,7 @@ __global__ void __launch_bounds__(kTileThreads,
         return;
     }
 
-    if (warp == kTileConsumerWarps) {
+    if (warp == CW) {
         if (lane != 0) return;
         // ---------------- producer ----------------
         int k = 0;
@@ -516,7 +525,7 @@ __global__ void __launch_bounds__(kTileThreads,
             if (!item_at(g, i, step, t)) continue;
             const int st = k % NS;
             const uint32_t ph = (uint32_t)(k / NS) & 1u;
-            const TilePos q = tile_pos<S>(g, t);
+            const TilePos q = tile_pos<TS::W>(g, t);
             const TileEntry& E = g.e[q.e];
             const int nx = E.a.nx, ny = E.a.ny;
             if (step > 0) {
@@ -606,7 +615,7 @@ __global__ void __launch_bounds__(kTileThreads,
         if (!item_at(g, i, step, t)) continue;
         const int st = k % NS;
         const uint32_t ph = (uint32_t)(k / NS) & 1u;
-        const TilePos q = tile_pos<S>(g, t);
+        const TilePos q = tile_pos<TS::W>(g, t);
         const TileEntry& E = g.e[q.e];
         S* dst = E.ring > 0 ? static_cast<S*>(const_cast<void*>(E.buf[0])) + (long long)(step + 1) * E.ring
                             : static_cast<S*>(const_cast<void*>(E.buf[(E.cur + step + 1) & 1]));
@@ -626,7 +635,9 @@ __global__ void __launch_bounds__(kTileThreads,
     }
 }
 
-// dynamic shared memory of tile_step_kernel<S, *, NS>
-template <typename S> constexpr int tile_smem_bytes(int ns) { return ns * Tile<S>::STAGE + 2 * ns * 8 + ns * 4; }
+// dynamic shared memory of tile_step_kernel<S, *, NS, FORM>
+template <typename S, int FORM> constexpr int tile_smem_bytes(int ns) {
+    return ns * Tile<S, TileForm<S, FORM>::CW>::STAGE + 2 * ns * 8 + ns * 4;
+}
 
 }  // namespace lbm

@@ -1,7 +1,8 @@
 // Bulk-copy staged step kernels for __half population storage, light form (BGK, RM, HM, PR).
 #include "lbm_tile_table.cuh"
-#include "lbm_internal.h"
 
 namespace lbm {
-const void* tile_kernel_f16_light(bool shifted, int stages) { return tile_kernel_table<__half, 1>(shifted, stages); }
+bool tile_kernel_f16_light(bool shifted, int stages, TileKernelInfo* out) {
+    return tile_kernel_info<__half, 1>(shifted, stages, out);
+}
 }  // namespace lbm

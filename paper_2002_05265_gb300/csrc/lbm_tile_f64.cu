@@ -1,7 +1,8 @@
-// Bulk-copy staged step kernels for double population storage.
+// Bulk-copy staged step kernels for double population storage (general form only).
 #include "lbm_tile_table.cuh"
-#include "lbm_internal.h"
 
 namespace lbm {
-const void* tile_kernel_f64(bool shifted, int stages, bool) { return tile_kernel_table<double, 0>(shifted, stages); }
+bool tile_kernel_f64(bool shifted, int stages, int form, TileKernelInfo* out) {
+    return form == 0 && tile_kernel_info<double, 0>(shifted, stages, out);
+}
 }  // namespace lbm

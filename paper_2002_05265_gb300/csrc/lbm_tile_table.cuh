@@ -1,7 +1,8 @@
-// Instantiates the bulk-copy staged step kernel for one storage type (stages 2, 3, 4; form 0
-// general, form 1 the light 16-bit form).
+// Instantiates the bulk-copy staged step kernel for one storage type and kernel form (stages
+// 2, 3, 4; both shift families) and describes it to the host.
 #pragma once
 #include "lbm_tile.cuh"
+#include "lbm_internal.h"
 
 namespace lbm {
 template <typename S, int FORM>
@@ -12,5 +13,13 @@ static const void* tile_kernel_table(bool shifted, int stages) {
         case 4: return shifted ? (const void*)tile_step_kernel<S, true, 4, FORM> : (const void*)tile_step_kernel<S, false, 4, FORM>;
         default: return nullptr;
     }
+}
+template <typename S, int FORM>
+static bool tile_kernel_info(bool shifted, int stages, TileKernelInfo* out) {
+    out->kernel = tile_kernel_table<S, FORM>(shifted, stages);
+    out->threads = TileForm<S, FORM>::THREADS;
+    out->width = Tile<S, TileForm<S, FORM>::CW>::W;
+    out->smem = tile_smem_bytes<S, FORM>(stages);
+    return out->kernel != nullptr;
 }
 }  // namespace lbm

@@ -18,6 +18,7 @@ LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = range(4)
 LBM_PRESET_SRT, LBM_PRESET_REG = 0, 1
 LBM_PATH_AUTO, LBM_PATH_VECTOR, LBM_PATH_BULK = 0, 1, 2
 LBM_ORDER_AUTO, LBM_ORDER_STEP, LBM_ORDER_WAVE, LBM_ORDER_BLOCK = 0, 1, 2, 3
+LBM_FORM_AUTO, LBM_FORM_GENERAL, LBM_FORM_LIGHT, LBM_FORM_WIDE = 0, 1, 2, 3
 LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_CUDA, LBM_ERR_BLOWUP, LBM_ERR_TIMEOUT, LBM_ERR_NOMEM = \
     0, -1, -2, -3, -4, -5, -6
 
@@ -70,6 +71,7 @@ _SIGNATURES = {
     "lbm_get_layout": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "lbm_set_kernel_path": (_I, [_P, _I, _I]),
     "lbm_set_launch_shape": (_I, [_P, _I, _I]),
+    "lbm_set_tile_form": (_I, [_P, _I]),
     "lbm_group_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _I]),
     "lbm_group_step": (_I, [_P, _LL]),
     "lbm_group_destroy": (None, [_P]),
@@ -227,6 +229,10 @@ def lbm_set_kernel_path(ctx, path, stages=0):
 
 def lbm_set_launch_shape(ctx, steps_per_launch=0, order=LBM_ORDER_AUTO):
     _check(load_library().lbm_set_launch_shape(ctx, steps_per_launch, order), ctx)
+
+
+def lbm_set_tile_form(ctx, form=LBM_FORM_AUTO):
+    _check(load_library().lbm_set_tile_form(ctx, form), ctx)
 
 
 def lbm_group_create(ctxs, graph_steps=64):
@@ -431,3 +437,6 @@ class Lattice:
 
     def set_launch_shape(self, steps_per_launch=0, order=LBM_ORDER_AUTO):
         lbm_set_launch_shape(self.ctx, steps_per_launch, order)
+
+    def set_tile_form(self, form=LBM_FORM_AUTO):
+        lbm_set_tile_form(self.ctx, form)

@@ -1,7 +1,9 @@
 """The two step-kernel families on lattices with several tiles per row and a short last tile:
 the copy-engine staged kernel (LBM_PATH_BULK, cp.async.bulk into a ring of 2-4 shared-memory
 stages) and the register-staged kernels (LBM_PATH_VECTOR), each against the FP64 oracle and
-against each other.  Tile widths: 512 (FP64), 1024 (FP32), 2048 (FP16, BF16) nodes."""
+against each other.  Tile widths of the copy-engine kernel's forms: general 512 (FP64), 1024
+(FP32), 2048 (FP16, BF16) nodes; light 512 (FP32), 2048 (16-bit); wide 2048 (FP32), 4096
+(16-bit)."""
 
 import numpy as np
 import pytest
@@ -320,9 +322,10 @@ def test_wavefront_order_fp64(L, model, shape, launch_steps):
 
 
 def test_launch_shapes_agree_bitwise(L):
-    """The launch shape only reorders the same per-tile arithmetic: one step per launch, step
-    order with 10 steps per launch, and the wavefront with 16 steps per launch give identical
-    FP32 populations (eight 256 x 160 lattices of all models in one group, 50 steps)."""
+    """The launch shape only reorders the same per-tile arithmetic: in the general kernel form,
+    one step per launch, step order with 10 steps per launch, the wavefront with 16 steps per
+    launch and the block order give identical FP32 populations (eight 256 x 160 lattices of all
+    models in one group, 50 steps)."""
     rates = olbm.rates_from_nu(1e-4, "reg")
     fields = flows.double_shear_layer(256, 160, Ma=0.1, width_frac=0.05)
     results = []
@@ -333,6 +336,7 @@ def test_launch_shapes_agree_bitwise(L):
             lat = L.Lattice(256, 160, L.MODELS[m], rates, storage=L.LBM_F32)
             lat.set_kernel_path(L.LBM_PATH_BULK)
             lat.set_launch_shape(steps, order)
+            lat.set_tile_form(L.LBM_FORM_GENERAL)
             lat.init_equilibrium(*_dev(*fields))
             lats.append(lat)
         g = L.lbm_group_create([x.ctx for x in lats], graph_steps=8)
@@ -396,3 +400,89 @@ def test_full_size_16384_reduced_precision_sampled(L, storage, tol):
         assert abs(float(uy[y, x]) - ry[P // 2, P // 2]) <= tol, (y, x)
     del ux, uy
     torch.cuda.empty_cache()
+
+
+_GENERAL_CACHE = {}
+_ORACLE_CACHE = {}
+
+
+def _run_group(L, fields, models, rates, storage, steps, form, launch_steps):
+    rho, ux, uy = fields
+    ny, nx = rho.shape
+    lats = []
+    for m in models:
+        lat = L.Lattice(nx, ny, L.MODELS[m], rates, storage=storage)
+        lat.set_kernel_path(L.LBM_PATH_BULK)
+        lat.set_launch_shape(launch_steps, L.LBM_ORDER_STEP)
+        lat.set_tile_form(form)
+        lat.init_equilibrium(*_dev(rho, ux, uy))
+        lats.append(lat)
+    g = L.lbm_group_create([x.ctx for x in lats], graph_steps=0)
+    L.lbm_group_step(g, steps)
+    out = {}
+    for m, lat in zip(models, lats):
+        assert lat.status()[0] == L.LBM_OK
+        f = torch.empty((9, ny, nx), dtype=torch.float64, device="cuda")
+        lat.get_populations(f)
+        out[m] = f.cpu().numpy()
+    L.lbm_group_destroy(g)
+    for lat in lats:
+        lat.close()
+    return out
+
+
+@pytest.mark.parametrize("launch_steps", [1, 6])
+@pytest.mark.parametrize("shape", [(4120, 3), (136, 21)])
+@pytest.mark.parametrize("form", ["light", "wide"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_kernel_forms_against_oracle_and_general_form(L, storage, form, shape, launch_steps):
+    """The light form (BGK, RM, HM, PR; FP32: 4 consumer warps at 3 CTAs per SM, 16-bit: the
+    packed 8-node pass) and the wide form (every model, 16 consumer warps at 1 CTA per SM) on a
+    group of lattices: 4120 x 3 (segment tiles of every form's width with a short last tile of
+    24 nodes) and 136 x 21 (row blocks of 3 to 30 rows, the last one short), one step per launch
+    and 6 steps per launch (row-completion counters), 60 steps.  FP32: within 1e-5 of the
+    oracle's velocity and within 1e-6 of the general form's populations; 16-bit: within the
+    storage-rounding bound of both."""
+    nx, ny = shape
+    st = L.STORAGES[storage]
+    models = ["bgk", "rm", "hm", "pr"] if form == "light" else MODELS
+    fields = flows.vortex(nx, ny, Ma=0.1, radius_frac=0.02 if nx > 1000 else 0.1, noise=1e-8, seed=nx + ny)
+    rates = olbm.rates_from_nu(1e-4, "srt")
+    f0 = olbm.init_equilibrium(*fields)
+    fm = L.LBM_FORM_LIGHT if form == "light" else L.LBM_FORM_WIDE
+    got = _run_group(L, fields, models, rates, st, 60, fm, launch_steps)
+    key = (storage, shape)
+    if key not in _GENERAL_CACHE:
+        _GENERAL_CACHE[key] = _run_group(L, fields, MODELS, rates, st, 60, L.LBM_FORM_GENERAL, 6)
+    gen = _GENERAL_CACHE[key]
+    bound = None if storage == "f32" else WALK_FACTOR * storage_walk_error(f0, storage, 60)
+    for m in models:
+        if (shape, m) not in _ORACLE_CACHE:
+            _ORACLE_CACHE[(shape, m)] = olbm.run(f0, m, rates, 60)
+        ref = _ORACLE_CACHE[(shape, m)]
+        if storage == "f32":
+            assert _vel_err(got[m], ref) <= 1e-5, m
+            assert float(np.max(np.abs(got[m] - gen[m]))) <= 1e-6, m
+        else:
+            assert _l2(got[m], ref) <= bound, m
+            assert _l2(got[m], gen[m]) <= bound, m
+
+
+def test_tile_form_argument_checks(L):
+    lat = L.Lattice(64, 64, L.LBM_CHM, (1.5, 1.5, 1.5), storage=L.LBM_F32)
+    for form in (-1, 4):
+        with pytest.raises(L.LBMError) as e:
+            lat.set_tile_form(form)
+        assert e.value.code == L.LBM_ERR_INVALID_ARG
+    with pytest.raises(L.LBMError) as e:
+        lat.set_tile_form(L.LBM_FORM_LIGHT)           # CHM is not a light model
+    assert e.value.code == L.LBM_ERR_UNSUPPORTED
+    lat.set_tile_form(L.LBM_FORM_WIDE)
+    lat.close()
+    lat = L.Lattice(64, 64, L.LBM_BGK, (1.5, 1.5, 1.5), storage=L.LBM_F64)
+    for form in (L.LBM_FORM_LIGHT, L.LBM_FORM_WIDE):  # FP64 has the general form only
+        with pytest.raises(L.LBMError) as e:
+            lat.set_tile_form(form)
+        assert e.value.code == L.LBM_ERR_UNSUPPORTED
+    lat.set_tile_form(L.LBM_FORM_GENERAL)
+    lat.close()
