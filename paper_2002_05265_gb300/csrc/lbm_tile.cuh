@@ -64,9 +64,10 @@ namespace lbm {
 //    multi-step launches (groups of small lattices, the adjoint's recomputation), where the
 //    row-counter waits want several CTAs per SM.
 //  * FORM 1, light: one-step launches whose lattices all run BGK, RM, HM or PR.  FP32: 4
-//    consumer warps and 2 CTAs per SM with 115 registers (tiles of 512 nodes; measured 1.02 of
-//    the copy bandwidth at 16384^2 and 1.01 at 4096^2, against 0.98-0.99 for 8 warps at 1 CTA
-//    per SM, 0.94 for 4 warps at 3 CTAs per SM with 96 registers, 0.95 for the general form).
+//    consumer warps and 2 CTAs per SM with 110-115 registers (tiles of 512 nodes; measured
+//    1.02 of the copy bandwidth at 16384^2 and 1.01 at 4096^2, against 0.98-0.99 for 8 warps
+//    at 1 CTA per SM, 0.94 for 4 warps at 3 CTAs per SM with 96 registers, 0.95 for the
+//    general form).
 //    16-bit: 8 consumer warps at 1 CTA per SM and one pass of 8 nodes per thread with the values
 //    kept packed (tile_collide_packed): 16-byte accesses and half the passes, which their short
 //    collision affords.  It is a separate kernel because the packed path's register pressure
@@ -454,10 +455,10 @@ __device__ __forceinline__ void tile_consume(const unsigned char* stage, S* dst,
 // Persistent: CTA b processes tiles b, b + gridDim.x, ...; warps 0 .. CW - 1 consume, warp CW
 // is the producer (one lane issues the copies), warp CW + 1 the signal warp.  NS = stages in
 // the ring; FORM as in TileForm.  Registers (no spills): general FP32 / 16-bit 96, wide 96,
-// light FP32 115, light 16-bit 168 (the packed pass; with 4 stages one CTA keeps as many bytes
-// in flight as two did with 2).  In a multi-step launch one CTA per SM stalls its SM at every
-// row-counter wait (0.49-0.83 against 0.71-0.97 for groups of eight 1024^2 lattices), hence
-// the single-CTA forms serve one-step launches.
+// light FP32 110-115, light 16-bit 168 (the packed pass; with 4 stages one CTA keeps as many
+// bytes in flight as two did with 2).  In a multi-step launch one CTA per SM stalls its SM at
+// every row-counter wait (0.49-0.83 against 0.71-0.97 for groups of eight 1024^2 lattices),
+// hence the single-CTA forms serve one-step launches.
 template <typename S, bool SHIFT, int NS, int FORM>
 __global__ void __launch_bounds__(TileForm<S, FORM>::THREADS, TileForm<S, FORM>::MINB)
     tile_step_kernel(const __grid_constant__ TileArgs g) {
