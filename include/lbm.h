@@ -284,11 +284,12 @@ int lbm_set_launch_shape(lbm_ctx* ctx, int steps_per_launch, int order);
  *                     2 CTAs per SM; 16-bit: 8 consumer warps, 1 CTA per SM, 8 nodes a thread.
  *   LBM_FORM_WIDE     every model, FP32 / FP16 / BF16; 16 consumer warps, 1 CTA per SM.
  *   LBM_FORM_AUTO     the default: the light form when every lattice of the group runs BGK, RM,
- *                     HM or PR, else the wide form, one time step per launch, where a time step
- *                     has at least 24 of the form's tiles per resident CTA (or one step per
- *                     launch is asked for with lbm_set_launch_shape), except that a single
- *                     lattice the general form would advance in the wavefront order keeps the
- *                     general form; the general form otherwise (and for FP64).
+ *                     HM or PR in FP32 or FP16 storage, else the wide form, one time step per
+ *                     launch, where a time step has at least 24 of the form's tiles per
+ *                     resident CTA (or one step per launch is asked for with
+ *                     lbm_set_launch_shape), except that a single lattice the general form
+ *                     would advance in the wavefront order keeps the general form; the general
+ *                     form otherwise (and for FP64).
  * Applies to the context's next lbm_step and to groups created afterwards (a group takes the
  * form of its first context when its lattices allow it, else LBM_FORM_AUTO).  Errors:
  * LBM_ERR_INVALID_ARG for an unknown form; LBM_ERR_UNSUPPORTED for LBM_FORM_LIGHT on another

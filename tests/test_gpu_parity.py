@@ -321,6 +321,42 @@ def test_conservation(L, storage):
         assert np.all(drift <= bound), (drift, bound)
 
 
+def test_group_checks_equal_individual_checks(L):
+    """Blow-up checks of a group's lattices that fall due together run concurrently (one
+    stream each, joined back to the group's stream): five 32 x 32 FP32 lattices with check
+    cadences 50, 50, 100, 0 and 50 (two unstable, Ma = 0.9; one with the kinetic-energy
+    criterion), 1000 steps in graph chunks of 10, give the same status, blow-up step and
+    reductions as each lattice stepped alone."""
+    n = 32
+    specs = [("bgk", 0.9, 1e-6, 50, 0.0), ("rr", 0.1, 1e-2, 50, 0.0), ("chm", 0.1, 1e-3, 100, 0.0),
+             ("k", 0.1, 1e-3, 0, 0.0), ("hm", 0.9, 1e-6, 50, 1e-3)]
+
+    def make(m, ma, nu, every, ke):
+        lat = L.Lattice(n, n, L.MODELS[m], olbm.rates_from_nu(nu), storage=L.LBM_F32)
+        lat.init_equilibrium(*_dev(*flows.uniform_noise(n, Ma=ma, amp=1e-3, seed=3)))
+        lat.set_check(every, ke_ref=ke)
+        return lat
+
+    grp = [make(*sp) for sp in specs]
+    alone = [make(*sp) for sp in specs]
+    g = L.lbm_group_create([x.ctx for x in grp], graph_steps=10)
+    L.lbm_group_step(g, 1000)
+    for a in alone:
+        a.step(1000)
+    blown = 0
+    for x, a in zip(grp, alone):
+        assert x.status() == a.status()
+        blown += x.status()[0] == L.LBM_ERR_BLOWUP
+        ra, rb = np.empty(8), np.empty(8)
+        x.reduce(ra)
+        a.reduce(rb)
+        assert np.array_equal(ra, rb, equal_nan=True)
+    assert blown >= 2
+    L.lbm_group_destroy(g)
+    for lat in grp + alone:
+        lat.close()
+
+
 def test_blowup_detection(L):
     """An unstable lattice (BGK, Ma = 0.9, nu = 1e-6) is flagged by the periodic check; a
     stable one is not; a NaN written from the host is caught at the next check."""
@@ -378,7 +414,8 @@ def test_full_size_double_shear_layer_sampled(L, model):
 def test_benchmark_group_configuration_sampled(L):
     """The benchmark's own launch configuration: the eight 1024 x 1024 FP32 double-shear-layer
     lattices (one per model, nu = 1e-5, BGK SRT and the others REG) in one group with 100-step
-    graph chunks, i.e. one copy-engine launch advancing all eight by 100 steps.  After those
+    graph chunks, i.e. 100 copy-engine launches (wide form) each advancing all eight by one
+    step.  After those
     100 steps, 2 sampled nodes per lattice (one at the periodic corner) agree with the oracle
     run on the (2k + 3)^2 light-cone patch around each node within 1e-5 on u."""
     N, k = 1024, 100
