@@ -370,11 +370,15 @@ cudaError_t launch_tile(lbm_group* g, const void* const* buf0, void* const* buf1
     cfg.blockDim = dim3(g->tthreads);
     cfg.dynamicSmemBytes = (size_t)g->tsmem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;   // CTAs of a multi-step launch wait on one another
     attr[0].val.cooperative = nsteps > 1 ? 1 : 0;
+    // one-step launches: programmatic dependent launch (the kernel's producer waits for the
+    // previous kernel on the stream before its first copy)
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = (LBM_TILE_PDL && nsteps == 1) ? 1 : 0;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     void* args[] = {(void*)&ta};
     return cudaLaunchKernelExC(&cfg, g->tkernel[sh], args);
 }

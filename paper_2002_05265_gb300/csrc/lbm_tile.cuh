@@ -85,6 +85,9 @@ namespace lbm {
 #ifndef LBM_TILE_HALF_CV
 #define LBM_TILE_HALF_CV 4
 #endif
+#ifndef LBM_TILE_PDL
+#define LBM_TILE_PDL 1   // programmatic dependent launch of one-step launches (see the kernel)
+#endif
 template <typename S, int FORM> struct TileForm {
     static constexpr int CW = FORM == 2 ? 16 : ((FORM == 1 && sizeof(S) == 4) ? 4 : 8);   // consumer warps
     static constexpr int MINB = sizeof(S) == 8 ? 1 : (FORM == 0 ? 2 : ((FORM == 1 && sizeof(S) == 4) ? 2 : 1));
@@ -476,6 +479,13 @@ __global__ void __launch_bounds__(TileForm<S, FORM>::THREADS, TileForm<S, FORM>:
             done[s] = 0u;
         }
         mbar_init_fence();
+#if LBM_TILE_PDL
+        // A one-step launch is made with programmatic stream serialization: the next step's
+        // launch may be scheduled now; its CTAs take the SM slots this launch's CTAs free as
+        // they exit (every form fills its SMs' registers or shared memory, so none start
+        // earlier), overlapping its launch and set-up with this launch's last tiles.
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
     }
     __syncthreads();
     // CTA b takes work items b, b + gridDim.x, ... (all three roles in the same order)
@@ -518,6 +528,13 @@ __global__ void __launch_bounds__(TileForm<S, FORM>::THREADS, TileForm<S, FORM>:
     if (warp == CW) {
         if (lane != 0) return;
         // ---------------- producer ----------------
+#if LBM_TILE_PDL
+        // Wait until the previous kernel on the stream has completed and its writes are
+        // visible (immediate when this launch was not made with programmatic serialization).
+        // Every global access of this CTA comes after it: the consumers and the signal warp
+        // touch global memory only for tiles whose copies this thread issues afterwards.
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
         int k = 0;
         bool ok = true;
         for (unsigned i = blockIdx.x; i < items; i += gridDim.x) {
