@@ -480,13 +480,35 @@ int launch_check(lbm_ctx* c, double* out8_dev, int apply, cudaStream_t s = nullp
     return LBM_OK;
 }
 
-// The blow-up checks of several contexts of a group that fall due together run concurrently,
-// each on its own stream forked from and joined back to the group's stream: one check is a
+// The blow-up checks of several contexts of a group that fall due together: one check is a
 // short, single-wave reduction (about 23 us for a 1024^2 FP32 lattice, SMs 59 % active), so
-// run one after another they leave most of the GPU idle.  Each context has its own scratch,
-// result and status words, so the checks share nothing.
+// run one after another they leave most of the GPU idle.  Contexts of one storage type share
+// one launch (lbm::launch_reduce_group, each context's results bitwise those of its own
+// check); otherwise each check runs on its own stream forked from and joined back to the
+// group's stream.  Each context has its own scratch, result and status words.
 int launch_checks(lbm_group* g, const std::vector<lbm_ctx*>& due) {
     lbm_ctx* c0 = g->ctx[0];
+    bool one = due.size() >= 2 && due.size() <= (size_t)lbm::kReduceGroupMax;
+    for (lbm_ctx* c : due) one = one && c->storage == due[0]->storage;
+    if (one) {
+        lbm::ReduceGroupArgs ra;
+        ra.n = (int)due.size();
+        for (size_t k = 0; k < due.size(); ++k) {
+            lbm_ctx* c = due[k];
+            lbm::ReduceJob& J = ra.j[k];
+            J.buf = c->buf[c->cur];
+            J.a = field_args(c);
+            J.partials = c->partials;
+            J.counter = reinterpret_cast<unsigned*>(c->partials + 8 * lbm::reduce_blocks());
+            J.out = c->red_out;
+            J.status = c->status;
+            J.blowup_step = c->blowup_step;
+            J.c.ke_ref = c->ke_ref; J.c.ke_factor = c->ke_factor; J.c.uref_x = c->uref_x; J.c.uref_y = c->uref_y;
+            J.c.step = c->steps; J.c.apply = 1;
+        }
+        LBM_CK(c0, lbm::launch_reduce_group(due[0]->storage, ra, g->stream));
+        return LBM_OK;
+    }
     if (due.size() < 2) {
         for (lbm_ctx* c : due) {
             int rc = launch_check(c, c->red_out, 1);

@@ -287,10 +287,11 @@ __device__ __forceinline__ void reduce_epilogue(double (&acc)[kReduceValues], do
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
     __syncthreads();
-    if (!last) return;
-    __threadfence();   // every block's partials after the count
-    finish_fold(partials, gridDim.x, a, out, status, blowup_step, c);
-    if (threadIdx.x == 0) *counter = 0u;
+    if (last) {        // uniform over the block
+        __threadfence();   // every block's partials after the count
+        finish_fold(partials, gridDim.x, a, out, status, blowup_step, c);
+        if (threadIdx.x == 0) *counter = 0u;
+    }
 }
 
 // Pass 1, scalar-load form for layouts whose rows are not 16-byte aligned (caller-owned
@@ -333,9 +334,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel_scalar(const S* 
 // Pass 1: the same vectorised pull gather as the step kernel, one row segment per thread and
 // iteration.
 template <typename S, bool FUSED>
-__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const S* buf, FieldArgs a, double* partials,
-                                                                unsigned* counter, double* out, int* status,
-                                                                long long* blowup_step, CheckArgs c) {
+__device__ __forceinline__ void reduce_pass1(const S* buf, const FieldArgs& a, double* partials, unsigned* counter,
+                                             double* out, int* status, long long* blowup_step, const CheckArgs& c) {
     using T = typename Conv<S>::T;
     constexpr int VEC = DefaultVec<S>::value;
     const int lane = threadIdx.x & 31;
@@ -367,6 +367,26 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const S* buf, Fi
     segment_flush(p, acc);
     acc[7] = (double)p.bad;
     reduce_epilogue<FUSED>(acc, partials, counter, a, out, status, blowup_step, c);
+}
+template <typename S, bool FUSED>
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const S* buf, FieldArgs a, double* partials,
+                                                                unsigned* counter, double* out, int* status,
+                                                                long long* blowup_step, CheckArgs c) {
+    reduce_pass1<S, FUSED>(buf, a, partials, counter, out, status, blowup_step, c);
+}
+
+// The checks of several lattices of one storage type in one launch: grid row blockIdx.y runs
+// job blockIdx.y's single-lattice check (reduce_kernel<S, true>) with the same kReduceBlocks
+// blocks and per-thread work, so every job's partials, fold order and results are bitwise
+// those of its own launch.  All jobs' blocks share the SMs, instead of one lattice's single
+// wave ramping up and draining at a time.  (Measured alternative: each block running every
+// job in turn was slower than separate launches on concurrent streams, 155 against 98 us for
+// eight 1024^2 FP32 lattices.)
+template <typename S>
+__global__ void __launch_bounds__(kReduceThreads) reduce_group_kernel(const __grid_constant__ ReduceGroupArgs g) {
+    const ReduceJob& J = g.j[blockIdx.y];
+    reduce_pass1<S, true>(static_cast<const S*>(J.buf), J.a, J.partials, J.counter, J.out, J.status, J.blowup_step,
+                          J.c);
 }
 
 // Pass 2 as its own launch (the allocation-free entry point, which keeps no counter).
@@ -446,6 +466,17 @@ cudaError_t reduce_t(const void* buf, const FieldArgs& a, double* partials, unsi
 
 }  // namespace
 
+template <typename S>
+cudaError_t reduce_group_t(const ReduceGroupArgs& g, cudaStream_t s) {
+    for (int e = 0; e < g.n; ++e) {
+        const ReduceJob& J = g.j[e];
+        if (((size_t)J.a.pitch * sizeof(S)) % 16 != 0 || ((uintptr_t)J.buf % 16) != 0 || !J.counter)
+            return cudaErrorInvalidValue;
+    }
+    reduce_group_kernel<S><<<dim3(kReduceBlocks, g.n), kReduceThreads, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
 int reduce_blocks() { return kReduceBlocks; }
 size_t reduce_scratch_bytes() { return sizeof(double) * kReduceValues * kReduceBlocks + 16; }
 
@@ -472,6 +503,11 @@ cudaError_t launch_gather(int storage, const void* buf, const FieldArgs& a, doub
 cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, double* partials, unsigned* counter,
                           double* out8, int* status, long long* blowup_step, const CheckArgs& c, cudaStream_t s) {
     LBM_DISPATCH(storage, reduce_t<S>(buf, a, partials, counter, out8, status, blowup_step, c, s));
+}
+
+cudaError_t launch_reduce_group(int storage, const ReduceGroupArgs& g, cudaStream_t s) {
+    if (g.n < 1 || g.n > kReduceGroupMax) return cudaErrorInvalidValue;
+    LBM_DISPATCH(storage, reduce_group_t<S>(g, s));
 }
 
 cudaError_t launch_halo(int storage, void* buf, const FieldArgs& a, void* up, void* down, bool pack, cudaStream_t s) {

@@ -77,6 +77,25 @@ size_t reduce_scratch_bytes();
 cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, double* partials, unsigned* counter,
                           double* out8, int* status, long long* blowup_step, const CheckArgs& c,
                           cudaStream_t s);
+// The fused checks (with completion counters) of up to kReduceGroupMax lattices of one
+// storage type, 16-byte aligned rows, in one launch; each job's results are bitwise those of
+// its own launch_reduce.  cudaErrorInvalidValue for an unaligned job or a missing counter.
+constexpr int kReduceGroupMax = 16;
+struct ReduceJob {
+    const void* buf;
+    FieldArgs a;
+    double* partials;
+    unsigned* counter;
+    double* out;
+    int* status;
+    long long* blowup_step;
+    CheckArgs c;
+};
+struct ReduceGroupArgs {
+    int n;
+    ReduceJob j[kReduceGroupMax];
+};
+cudaError_t launch_reduce_group(int storage, const ReduceGroupArgs& g, cudaStream_t s);
 
 // Halo rows of a y-slab (lbm_halo_pack / lbm_halo_unpack): messages of [3][nx] raw storage
 // elements; pack reads rows ny - 2 (planes 2, 5, 6 -> up) and 1 (planes 4, 7, 8 -> down), unpack

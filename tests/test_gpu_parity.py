@@ -321,18 +321,19 @@ def test_conservation(L, storage):
         assert np.all(drift <= bound), (drift, bound)
 
 
-def test_group_checks_equal_individual_checks(L):
-    """Blow-up checks of a group's lattices that fall due together run concurrently (one
-    stream each, joined back to the group's stream): five 32 x 32 FP32 lattices with check
-    cadences 50, 50, 100, 0 and 50 (two unstable, Ma = 0.9; one with the kinetic-energy
-    criterion), 1000 steps in graph chunks of 10, give the same status, blow-up step and
-    reductions as each lattice stepped alone."""
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_group_checks_equal_individual_checks(L, storage):
+    """Blow-up checks of a group's lattices that fall due together run in one launch (each
+    lattice's check with its own grid-wide fold, bitwise as in its own launch): five 32 x 32
+    lattices with check cadences 50, 50, 100, 0 and 50 (two unstable, Ma = 0.9; one with the
+    kinetic-energy criterion), 1000 steps in graph chunks of 10, give the same status, blow-up
+    step and reductions as each lattice stepped alone."""
     n = 32
     specs = [("bgk", 0.9, 1e-6, 50, 0.0), ("rr", 0.1, 1e-2, 50, 0.0), ("chm", 0.1, 1e-3, 100, 0.0),
              ("k", 0.1, 1e-3, 0, 0.0), ("hm", 0.9, 1e-6, 50, 1e-3)]
 
     def make(m, ma, nu, every, ke):
-        lat = L.Lattice(n, n, L.MODELS[m], olbm.rates_from_nu(nu), storage=L.LBM_F32)
+        lat = L.Lattice(n, n, L.MODELS[m], olbm.rates_from_nu(nu), storage=L.STORAGES[storage])
         lat.init_equilibrium(*_dev(*flows.uniform_noise(n, Ma=ma, amp=1e-3, seed=3)))
         lat.set_check(every, ke_ref=ke)
         return lat
