@@ -399,6 +399,14 @@ def vortex_on_device(n, Ma, slab=1024):
     return out
 
 
+def form_name(lbm, g):
+    """Kernel family and form the library chose for a group (lbm_group_describe)."""
+    d = lbm.lbm_group_describe(g)
+    if d["family"] != lbm.LBM_PATH_BULK:
+        return "register-staged"
+    return {lbm.LBM_FORM_GENERAL: "general", lbm.LBM_FORM_LIGHT: "light", lbm.LBM_FORM_WIDE: "wide"}[d["form"]]
+
+
 def per_model_big(lbm, stream, peak, n=BIG_L, warmup=16, steps=48):
     """Throughput of every collision model x storage type on one n x n lattice: the
     convected vortex at Ma = 0.2, nu = 1e-6 (BGK single-rate, the others with equilibrated
@@ -426,7 +434,7 @@ def per_model_big(lbm, stream, peak, n=BIG_L, warmup=16, steps=48):
             t = rms / 1e3 / nl
             gbs = BYTES_PER_LU[s] * n * n / t / 1e9
             res[s][m] = {"glups": n * n / t / 1e9, "alg_gbs": gbs, "frac": gbs / peak,
-                         "launches": nk, "status": lat.status()[0]}
+                         "launches": nk, "status": lat.status()[0], "form": form_name(lbm, g)}
             lbm.lbm_group_destroy(g)
             lat.close()
     del fields
@@ -1050,9 +1058,13 @@ def main():
     avg_launch_s = replay_ms / 1e3 / kernel_launches
     bytes_per_launch = BYTES_PER_LU["f32"] * L * L * lattice_steps / kernel_launches
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    bulk = args.path != "vector"   # 1024 * 4 B rows: the bulk-copy kernel unless told otherwise
-    traffic = ncu_traffic("f32_tile_8x1024" if bulk else "f32_group_8x1024")
-    kname = ("lbm::tile_step_kernel<float> (cp.async.bulk ring)" if bulk
+    form = form_name(lbm, group)
+    bulk = form != "register-staged"
+    # the committed ncu traffic records: the wide form (the default here) and the
+    # register-staged group kernel
+    traffic = ncu_traffic("f32_tile_8x1024") if form == "wide" else (
+        ncu_traffic("f32_group_8x1024") if not bulk else None)
+    kname = (f"lbm::tile_step_kernel<float> (cp.async.bulk ring, {form} form)" if bulk
              else "lbm::group_step_kernel<float> (register-staged)")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind, "launch_us": avg_launch_s * 1e6,
@@ -1060,11 +1072,11 @@ def main():
                 "kernel": kname + f": one launch = {lattice_steps // kernel_launches // len(MODELS)} time step(s) "
                           "of the 8 lattices, 72 B per lattice update"}
 
-    # step-kernel launches counted by the group's replay timing (one multi-step launch per
-    # replay for the bulk-copy kernel, one per time step otherwise), plus per lattice: the
-    # equilibrium init, one reduction kernel per check (its last block folds the partials),
-    # the moments gather
-    launches_per_step = kernel_launches // args.steps + len(MODELS) * (1 + (S // CHECK_EVERY) + 1)
+    # step-kernel launches counted by the group's replay timing, plus one reduction launch per
+    # check of the eight lattices (they fall due together and share a launch; each lattice's
+    # last block folds its partials), and per lattice the equilibrium init and the moments
+    # gather
+    launches_per_step = kernel_launches // args.steps + S // CHECK_EVERY + 2 * len(MODELS)
 
     e2e = None
     if not args.no_e2e:

@@ -311,6 +311,16 @@ void lbm_group_destroy(lbm_group* g);
  * launch per time step; otherwise each context gets its own launch. */
 int lbm_group_set_timing(lbm_group* g, int enable);
 int lbm_group_timing(lbm_group* g, double* replay_ms, long long* lattice_steps, long long* kernel_launches);
+/* How the group is advanced (library design choice; the paper has no counterpart): *family =
+ * LBM_PATH_BULK (copy-engine staged launches over all contexts), or LBM_PATH_VECTOR
+ * (register-staged: one multi-lattice launch per step, or one launch per context and step);
+ * for LBM_PATH_BULK, *form = LBM_FORM_GENERAL / LBM_FORM_LIGHT / LBM_FORM_WIDE, *steps_per_launch
+ * the time steps of one launch, *tiles the tiles of one time step, *grid the resident CTAs a
+ * launch may use and *block the CTA size; for LBM_PATH_VECTOR those four are 0 and *form is
+ * LBM_FORM_AUTO.  Any pointer may be
+ * NULL.  Errors: LBM_ERR_INVALID_ARG for a null group. */
+int lbm_group_describe(const lbm_group* g, int* family, int* form, int* steps_per_launch, int* tiles, int* grid,
+                       int* block);
 
 /* Discrete adjoint of N steps (Eq. StreamCollide): lambda^n = dL/df^n runs backwards as
  *   lambda^n_j(x) = sum_i lambda^{n+1}_i(x + xi_i) dC_i/df_j(f^n(x))

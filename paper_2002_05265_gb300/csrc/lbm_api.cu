@@ -1142,6 +1142,20 @@ int lbm_group_set_timing(lbm_group* g, int enable) {
     return LBM_OK;
 }
 
+int lbm_group_describe(const lbm_group* g, int* family, int* form, int* steps_per_launch, int* tiles, int* grid,
+                       int* block) {
+    if (!g) return LBM_ERR_INVALID_ARG;
+    const bool bulk = g->tiled && tile_shift(g) >= 0;
+    if (family) *family = bulk ? LBM_PATH_BULK : LBM_PATH_VECTOR;
+    if (form) *form = bulk ? (g->tform == 0 ? LBM_FORM_GENERAL : (g->tform == 1 ? LBM_FORM_LIGHT : LBM_FORM_WIDE))
+                           : LBM_FORM_AUTO;
+    if (steps_per_launch) *steps_per_launch = bulk ? tile_steps_per_launch(g) : 0;
+    if (tiles) *tiles = bulk ? (int)g->ttotal : 0;
+    if (grid) *grid = bulk ? std::max(g->tgrid[0], g->tgrid[1]) : 0;
+    if (block) *block = bulk ? g->tthreads : 0;
+    return LBM_OK;
+}
+
 int lbm_group_timing(lbm_group* g, double* replay_ms, long long* lattice_steps, long long* kernel_launches) {
     if (!g) return LBM_ERR_INVALID_ARG;
     lbm_ctx* c0 = g->ctx[0];

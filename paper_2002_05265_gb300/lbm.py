@@ -72,6 +72,7 @@ _SIGNATURES = {
     "lbm_set_kernel_path": (_I, [_P, _I, _I]),
     "lbm_set_launch_shape": (_I, [_P, _I, _I]),
     "lbm_set_tile_form": (_I, [_P, _I]),
+    "lbm_group_describe": (_I, [_P] + [ctypes.POINTER(_I)] * 6),
     "lbm_group_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _I]),
     "lbm_group_step": (_I, [_P, _LL]),
     "lbm_group_destroy": (None, [_P]),
@@ -233,6 +234,17 @@ def lbm_set_launch_shape(ctx, steps_per_launch=0, order=LBM_ORDER_AUTO):
 
 def lbm_set_tile_form(ctx, form=LBM_FORM_AUTO):
     _check(load_library().lbm_set_tile_form(ctx, form), ctx)
+
+
+def lbm_group_describe(g):
+    """How a group is advanced: dict of family (LBM_PATH_*), form (LBM_FORM_*),
+    steps_per_launch, tiles, grid, block."""
+    vals = [ctypes.c_int(0) for _ in range(6)]
+    rc = load_library().lbm_group_describe(g, *[ctypes.byref(v) for v in vals])
+    if rc != LBM_OK:
+        raise LBMError(rc, "lbm_group_describe failed")
+    keys = ("family", "form", "steps_per_launch", "tiles", "grid", "block")
+    return {k: v.value for k, v in zip(keys, vals)}
 
 
 def lbm_group_create(ctxs, graph_steps=64):

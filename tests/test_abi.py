@@ -76,3 +76,12 @@ def test_error_strings(lib):
     from paper_2002_05265_gb300 import lbm
     assert lbm.load_library().lbm_error_string(-4) == b"blow-up detected"
     assert b"sm_103a" in lib.lbm_version()
+
+
+def test_null_handles_are_rejected(lib):
+    """The launch-shape calls check their handles on the host (no GPU needed)."""
+    n = ctypes.c_int(7)
+    assert lib.lbm_set_tile_form(None, 0) == -1
+    assert lib.lbm_set_launch_shape(None, 0, 0) == -1
+    assert lib.lbm_group_describe(None, ctypes.byref(n), None, None, None, None, None) == -1
+    assert n.value == 7

@@ -486,3 +486,40 @@ def test_tile_form_argument_checks(L):
         assert e.value.code == L.LBM_ERR_UNSUPPORTED
     lat.set_tile_form(L.LBM_FORM_GENERAL)
     lat.close()
+
+
+def test_default_kernel_form_choice(L):
+    """The library's default form and launch shape for the configurations it was measured on
+    (lbm_group_describe): the benchmark's eight 1024^2 FP32 lattices of all models run the
+    wide form one step per launch; four of them (fewer than 24 wide tiles per CTA) the general
+    form many steps per launch; a 4096^2 BGK lattice the light form; a 4096^2 CHM lattice the
+    general form's 16-step wavefront launches; BF16 BGK lattices the wide form; FP64 the
+    general form; a 64^2 lattice (fewer tiles than CTAs) the register-staged kernels."""
+    rates = (1.5, 1.5, 1.5)
+
+    def describe(specs, storage=None):
+        st = L.LBM_F32 if storage is None else storage
+        lats = [L.Lattice(n, n, L.MODELS[m], rates, storage=st) for n, m in specs]
+        g = L.lbm_group_create([x.ctx for x in lats], graph_steps=0)
+        d = L.lbm_group_describe(g)
+        L.lbm_group_destroy(g)
+        for lat in lats:
+            lat.close()
+        return d
+
+    d = describe([(1024, m) for m in MODELS])
+    assert (d["family"], d["form"], d["steps_per_launch"], d["tiles"], d["block"]) == \
+        (L.LBM_PATH_BULK, L.LBM_FORM_WIDE, 1, 8 * 512, 576)
+    d = describe([(1024, m) for m in MODELS[:4]])
+    assert (d["family"], d["form"], d["block"]) == (L.LBM_PATH_BULK, L.LBM_FORM_GENERAL, 320)
+    assert d["steps_per_launch"] > 1
+    d = describe([(4096, "bgk")])
+    assert (d["form"], d["steps_per_launch"], d["tiles"], d["block"]) == (L.LBM_FORM_LIGHT, 1, 4096 * 8, 192)
+    d = describe([(4096, "chm")])
+    assert (d["form"], d["steps_per_launch"]) == (L.LBM_FORM_GENERAL, 16)
+    d = describe([(4096, "bgk"), (4096, "pr")], storage=L.LBM_BF16)
+    assert (d["form"], d["steps_per_launch"]) == (L.LBM_FORM_WIDE, 1)
+    d = describe([(4096, "bgk")], storage=L.LBM_F64)
+    assert d["form"] == L.LBM_FORM_GENERAL
+    d = describe([(64, "bgk")])
+    assert (d["family"], d["form"], d["tiles"]) == (L.LBM_PATH_VECTOR, L.LBM_FORM_AUTO, 0)
