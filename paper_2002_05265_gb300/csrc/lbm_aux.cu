@@ -1,6 +1,7 @@
 // Auxiliary kernels: equilibrium initialisation, population scatter / gather, moments and
 // the FP64 global reductions behind the blow-up check.  None of these is on the per-step
 // hot path except the reduction, which runs every `check_every` steps.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -16,6 +17,11 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kReduceBlocks = 608;   // 4 x 152 SMs; fixed, so the fold order is deterministic
+#ifndef LBM_REDUCE_GROUP_BLOCKS
+#define LBM_REDUCE_GROUP_BLOCKS 76   // least blocks per lattice in a group's check launch
+#endif
+static_assert(LBM_REDUCE_GROUP_BLOCKS >= 1 && LBM_REDUCE_GROUP_BLOCKS <= kReduceBlocks,
+              "a group check's partials must fit a context's kReduceBlocks slots");
 constexpr int kReduceThreads = 128;  // threads of a reduction block (fewer threads, less FP64 folding)
 constexpr int kReduceValues = 8;
 constexpr int kReduceFlush = 4;      // row segments summed in the collision precision per FP64 add
@@ -376,12 +382,15 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const S* buf, Fi
 }
 
 // The checks of several lattices of one storage type in one launch: grid row blockIdx.y runs
-// job blockIdx.y's single-lattice check (reduce_kernel<S, true>) with the same kReduceBlocks
-// blocks and per-thread work, so every job's partials, fold order and results are bitwise
-// those of its own launch.  All jobs' blocks share the SMs, instead of one lattice's single
-// wave ramping up and draining at a time.  (Measured alternative: each block running every
-// job in turn was slower than separate launches on concurrent streams, 155 against 98 us for
-// eight 1024^2 FP32 lattices.)
+// job blockIdx.y's check (the code of reduce_kernel<S, true>) with kReduceBlocks / n blocks
+// (at least LBM_REDUCE_GROUP_BLOCKS) instead of kReduceBlocks: the jobs' blocks together fill
+// the SMs about as one lattice's check does, and fewer threads, each summing more row
+// segments, spend fewer FP64 folds, which bound the check (GB300's FP64 pipe).  The fold order
+// is fixed for a given group size, so a lattice's figures are reproducible; they differ from
+// its single-launch check only in the rounding of the FP64 sums.  Measured on eight 1024^2
+// FP32 lattices (the benchmark's step time outside the step kernel, per check of the eight):
+// 76 blocks each 82 us, 152: 90 us, 304: 94 us, 608: 104 us; each block running every job in
+// turn 155 us.
 template <typename S>
 __global__ void __launch_bounds__(kReduceThreads) reduce_group_kernel(const __grid_constant__ ReduceGroupArgs g) {
     const ReduceJob& J = g.j[blockIdx.y];
@@ -473,7 +482,8 @@ cudaError_t reduce_group_t(const ReduceGroupArgs& g, cudaStream_t s) {
         if (((size_t)J.a.pitch * sizeof(S)) % 16 != 0 || ((uintptr_t)J.buf % 16) != 0 || !J.counter)
             return cudaErrorInvalidValue;
     }
-    reduce_group_kernel<S><<<dim3(kReduceBlocks, g.n), kReduceThreads, 0, s>>>(g);
+    const int blocks = std::max(LBM_REDUCE_GROUP_BLOCKS, kReduceBlocks / g.n);
+    reduce_group_kernel<S><<<dim3(blocks, g.n), kReduceThreads, 0, s>>>(g);
     return cudaGetLastError();
 }
 

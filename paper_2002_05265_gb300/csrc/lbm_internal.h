@@ -78,8 +78,9 @@ cudaError_t launch_reduce(int storage, const void* buf, const FieldArgs& a, doub
                           double* out8, int* status, long long* blowup_step, const CheckArgs& c,
                           cudaStream_t s);
 // The fused checks (with completion counters) of up to kReduceGroupMax lattices of one
-// storage type, 16-byte aligned rows, in one launch; each job's results are bitwise those of
-// its own launch_reduce.  cudaErrorInvalidValue for an unaligned job or a missing counter.
+// storage type, 16-byte aligned rows, in one launch; each job's results are those of its own
+// launch_reduce up to the rounding of the FP64 sums (fewer blocks per job, a fixed fold order).
+// cudaErrorInvalidValue for an unaligned job or a missing counter.
 constexpr int kReduceGroupMax = 16;
 struct ReduceJob {
     const void* buf;
