@@ -1017,10 +1017,11 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
         // PR in FP32 / FP16, else wide; BF16 light models measured 0.99-1.00 of the copy
         // bandwidth at 16384^2 in the wide form, 0.965-0.98 in the light one) when one step per
         // launch is asked for, or when a step has at least LBM_ONE_STEP_TILES_PER_CTA of that
-        // form's tiles per resident CTA and no multi-step work order is asked for -- except that the wide form leaves a single lattice to the
-        // general form's wavefront launches where those apply (measured, FP32: 4096^2 0.96 of
-        // the copy bandwidth in the wavefront against 0.91 in the wide form; 8192^2 wide 0.96
-        // against 0.94 for the general form's one-step launches); otherwise the general form.
+        // form's tiles per resident CTA and no multi-step work order is asked for -- except
+        // that the wide form leaves a single lattice to the general form's wavefront launches
+        // where those apply (measured, FP32: 4096^2 0.96 of the copy bandwidth in the wavefront
+        // against 0.91 in the wide form; 8192^2 wide 0.96 against 0.94 for the general form's
+        // one-step launches); otherwise the general form.
         const bool light = storage != LBM_F64 && light_models(ctxs, n);
         const int one_form = storage == LBM_F64 ? -1 : ((light && storage != LBM_BF16) ? 1 : 2);
         const lbm_ctx* c0 = ctxs[0];
@@ -1041,6 +1042,7 @@ int lbm_group_create(lbm_group** out, lbm_ctx* const* ctxs, int n, int graph_ste
         }
         if (form < 0) form = 0;
         tile = plan(form);
+        if (!tile && form != 0) tile = plan(form = 0);   // a form that cannot be resident
         g->tone = tile && form != 0 ? 1 : 0;
         // the library's choice: a step with fewer tiles than resident CTAs leaves the copy
         // pipeline mostly idle (latency-bound); the register-staged kernels do better there
