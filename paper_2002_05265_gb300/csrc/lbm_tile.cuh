@@ -74,11 +74,13 @@ namespace lbm {
 //    makes the compiler spill in the loop every model shares (measured: the central-moment
 //    models then lose 2-4 %, and with 8 nodes at once themselves 3-6 %).
 //  * FORM 2, wide: every model, 16 consumer warps at 1 CTA per SM (tiles of 8 KB a plane).
-//    Serves one-step launches of the other groups: at 16384^2 the central-moment models run at
-//    0.98-0.99 (FP32) and 0.99-1.02 (16-bit) of the copy bandwidth, against 0.95-0.96 and
+//    Serves one-step launches of the other groups (and of BF16 light-model groups, 0.99-1.00
+//    against 0.965-0.98 in the light form): at 16384^2 the central-moment models run at
+//    0.98-1.01 (FP32) and 0.99-1.02 (16-bit) of the copy bandwidth, against 0.95-0.96 and
 //    0.96-0.99 in the general form; the benchmark's eight 1024^2 lattices one step per launch
-//    at 0.97, against 0.95 in the general form's 100-step launches.  In multi-step launches the
-//    single CTA stalls its SM at every row-counter wait (0.83), so those keep the general form.
+//    at 0.97-0.98, against 0.95 in the general form's 100-step launches.  In multi-step launches
+//    the single CTA stalls its SM at every row-counter wait (0.83), so those keep the general
+//    form.
 // Nodes a consumer thread collides per pass (one vector access per population): 16 bytes
 // for FP64 / FP32; for the 16-bit types LBM_TILE_HALF_CV nodes (4: 8-byte accesses, two
 // passes over a tile).
