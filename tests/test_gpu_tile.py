@@ -521,5 +521,34 @@ def test_default_kernel_form_choice(L):
     assert (d["form"], d["steps_per_launch"]) == (L.LBM_FORM_WIDE, 1)
     d = describe([(4096, "bgk")], storage=L.LBM_F64)
     assert d["form"] == L.LBM_FORM_GENERAL
+    d = describe([(4096, "bgk"), (4096, "hm")], storage=L.LBM_F16)
+    assert (d["form"], d["steps_per_launch"], d["block"]) == (L.LBM_FORM_LIGHT, 1, 320)
     d = describe([(64, "bgk")])
     assert (d["family"], d["form"], d["tiles"]) == (L.LBM_PATH_VECTOR, L.LBM_FORM_AUTO, 0)
+
+
+def test_forced_kernel_forms_are_honoured(L):
+    """lbm_set_tile_form on the first context decides the group's form where its lattices
+    allow it (and LBM_FORM_LIGHT on a group with a central-moment lattice falls back to the
+    default choice)."""
+    rates = (1.5, 1.5, 1.5)
+    cases = [(L.LBM_FORM_GENERAL, ["bgk", "cm"], L.LBM_FORM_GENERAL, 320),
+             (L.LBM_FORM_WIDE, ["bgk", "rm"], L.LBM_FORM_WIDE, 576),
+             (L.LBM_FORM_LIGHT, ["bgk", "pr"], L.LBM_FORM_LIGHT, 192)]
+    for form, models, want, block in cases:
+        lats = [L.Lattice(2048, 2048, L.MODELS[m], rates, storage=L.LBM_F32) for m in models]
+        lats[0].set_tile_form(form)
+        g = L.lbm_group_create([x.ctx for x in lats], graph_steps=0)
+        d = L.lbm_group_describe(g)
+        L.lbm_group_destroy(g)
+        assert (d["family"], d["form"], d["block"]) == (L.LBM_PATH_BULK, want, block), (form, d)
+        lats.append(L.Lattice(2048, 2048, L.LBM_CHM, rates, storage=L.LBM_F32))
+        g = L.lbm_group_create([x.ctx for x in lats], graph_steps=0)
+        d = L.lbm_group_describe(g)
+        L.lbm_group_destroy(g)
+        if form == L.LBM_FORM_LIGHT:
+            assert d["form"] != L.LBM_FORM_LIGHT
+        else:
+            assert d["form"] == want
+        for lat in lats:
+            lat.close()
