@@ -389,8 +389,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(const S* buf, Fi
 // is fixed for a given group size, so a lattice's figures are reproducible; they differ from
 // its single-launch check only in the rounding of the FP64 sums.  Measured on eight 1024^2
 // FP32 lattices (the benchmark's step time outside the step kernel, per check of the eight):
-// 76 blocks each 82 us, 152: 90 us, 304: 94 us, 608: 104 us; each block running every job in
-// turn 155 us.
+// 76 blocks each 82 us, 152: 90 us, 304: 94 us, 608: 104 us, 38: 120 us, 19: 210 us; each
+// block running every job in turn 155 us.
 template <typename S>
 __global__ void __launch_bounds__(kReduceThreads) reduce_group_kernel(const __grid_constant__ ReduceGroupArgs g) {
     const ReduceJob& J = g.j[blockIdx.y];
